@@ -1,0 +1,330 @@
+"""Pins of the oracle against what the paper and the mathematics fix (CPU only).
+
+Each test ties an oracle function to something other than the oracle itself: a table
+or byte string printed in the paper, a closed form, an algebraic identity, a library
+routine, a brute-force evaluation on tiny inputs, or a count with an independent
+formula.
+"""
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def _polymul(a, b):
+    out = [0] * (len(a) + len(b) - 1)
+    for i, x in enumerate(a):
+        for j, y in enumerate(b):
+            out[i + j] += x * y
+    return out
+
+
+def _coeff_list(p, q):
+    """Oracle coefficients as a dense list indexed by power of t."""
+    c = O.q_coefficients(p, q)
+    return [c.get(k, 0) for k in range(11)]
+
+
+# ---------------------------------------------------------------- Eq. 2.5 / Eq. 2.6
+
+def test_u11_matches_printed_table():
+    """Eq. 2.5: the 121 bits of u_11 printed in the paper."""
+    rows = _read_rows("u11_eq2_5.txt")
+    want = np.array([[int(ch) for ch in row] for row in rows], dtype=np.uint8)
+    assert want.shape == (11, 11)
+    assert np.array_equal(O.unsolvable_table(11), want)
+
+
+def test_u11_bytes_match_printed_packing():
+    """Eq. 2.6: the printed bytes of u_11 (highest bit leftmost, zero padding)."""
+    packed = O.pack_table_bytes(O.unsolvable_table(11))
+    assert len(packed) == 16
+    for row in _read_rows("u11_bytes_eq2_6.txt"):
+        idx, bits = row.split()
+        assert format(packed[int(idx)], "08b") == bits, idx
+
+
+@pytest.mark.parametrize("r", [2, 3, 5, 7])
+def test_small_prime_tables_vanish(r):
+    """Section 2, after Eq. 2.4: u_2, u_3, u_5 and u_7 are identically zero."""
+    assert int(O.unsolvable_table(r).sum()) == 0
+
+
+@pytest.mark.parametrize("r", [11, 13, 17, 19, 23, 29, 31])
+def test_pack_length_and_padding(r):
+    u = O.unsolvable_table(r)
+    b = O.pack_table_bytes(u)
+    assert len(b) == (r * r + 7) // 8
+    tail = (r * r) % 8
+    if tail:
+        assert b[-1] >> tail == 0
+    # unpack and compare bit by bit
+    bits = [(b[i // 8] >> (i % 8)) & 1 for i in range(r * r)]
+    assert bits == [int(x) for x in u.reshape(-1)]
+
+
+# ---------------------------------------------------------------- Eq. 1.1 closed forms
+
+def test_q11_closed_form():
+    """Q_{1,1}(t) = (t - 1)(t + 1)(t^2 + 1)^4."""
+    want = [1]
+    for f in ([-1, 1], [1, 1], [1, 0, 1], [1, 0, 1], [1, 0, 1], [1, 0, 1]):
+        want = _polymul(want, f)
+    assert _coeff_list(1, 1) == want
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 7, 12345])
+def test_q_p0_closed_form(p):
+    """Q_{p,0}(t) = t^6 (t - p^2)^2 (t + p^2)^2."""
+    want = [0, 0, 0, 0, 0, 0, 1]
+    for f in ([-p * p, 1], [-p * p, 1], [p * p, 1], [p * p, 1]):
+        want = _polymul(want, f)
+    assert _coeff_list(p, 0) == want
+
+
+@pytest.mark.parametrize("q", [1, 2, 5, 9, 4321])
+def test_q_0q_closed_form(q):
+    """Q_{0,q}(t) = t^6 (t^4 + 6 q^4 t^2 + q^8)."""
+    want = [0] * 6 + [q ** 8, 0, 6 * q ** 4, 0, 1]
+    assert _coeff_list(0, q) == want
+
+
+def test_evenness():
+    for p, q in [(2, 3), (5, 7), (100, 3), (65535, 4097)]:
+        c = _coeff_list(p, q)
+        assert all(c[k] == 0 for k in range(1, 11, 2))
+        for t in (1, 2, 17, 1000):
+            assert O.q_value(p, q, t) == O.q_value(p, q, -t)
+
+
+def test_weighted_homogeneity():
+    """Q_{lp,lq}(l^2 t) = l^20 Q_pq(t) (exact integers)."""
+    g = random.Random(1)
+    for _ in range(200):
+        p, q, t, lam = (g.randint(0, 10 ** 6), g.randint(0, 10 ** 6),
+                        g.randint(-10 ** 9, 10 ** 9), g.randint(1, 1000))
+        assert O.q_value(lam * p, lam * q, lam * lam * t) == lam ** 20 * O.q_value(p, q, t)
+
+
+def test_reflection():
+    """t^10 Q_pq(p^2 q^2 / t) = -p^10 q^10 Q_qp(t): coefficient of t^(10-k) on the left
+    is c_k(p, q) (pq)^(2k); on the right -(pq)^10 c_(10-k)(q, p)."""
+    g = random.Random(2)
+    for _ in range(200):
+        p, q = g.randint(1, 10 ** 5), g.randint(1, 10 ** 5)
+        a, b = _coeff_list(p, q), _coeff_list(q, p)
+        for k in range(11):
+            assert a[k] * (p * q) ** (2 * k) == -((p * q) ** 10) * b[10 - k]
+
+
+def test_diagonal_has_root():
+    """Q_{k,k}(k^2) = 0: the pairs p = q carry the integer root t = k^2."""
+    for k in list(range(1, 60)) + [2 ** 20 - 3, 2 ** 31 + 11]:
+        assert O.q_value(k, k, k * k) == 0
+
+
+def test_sympy_factorisation_consistent():
+    """Library cross-check: sympy factors Q_{k,k} with the root t = k^2 and finds Q_pq
+    irreducible for small coprime p != q (Conjecture 1.1)."""
+    sympy = pytest.importorskip("sympy")
+    t = sympy.symbols("t")
+
+    def poly(p, q):
+        return sum(c * t ** k for k, c in O.q_coefficients(p, q).items())
+
+    for k in (1, 2, 3):
+        _, fl = sympy.factor_list(poly(k, k))
+        assert any(sympy.degree(f, t) == 1 and f.subs(t, k * k) == 0 for f, _ in fl)
+    for p, q in [(2, 1), (3, 2), (5, 3), (7, 4)]:
+        _, fl = sympy.factor_list(poly(p, q))
+        assert len(fl) == 1 and fl[0][1] == 1 and sympy.degree(fl[0][0], t) == 10
+
+
+# ---------------------------------------------------------------- Definition 1.1 / Eq. 2.3
+
+@pytest.mark.parametrize("r", [2, 3, 5, 7, 11, 13])
+def test_table_vs_pure_python_definition(r):
+    """The numpy table equals Definition 1.1 evaluated pair by pair in pure Python."""
+    u = O.unsolvable_table(r)
+    for a in range(r):
+        for b in range(r):
+            assert u[a, b] == (0 if O.is_solvable(a, b, r) else 1)
+
+
+@pytest.mark.parametrize("r", W.first_odd_primes(24))
+def test_structural_zeros_and_symmetry(r):
+    """Row 0 and column 0 vanish (t = 0 is a root when pq = 0 mod r), the diagonals
+    p = +-q vanish (t = p^2 is a root), and u_r is symmetric (reflection identity)."""
+    u = O.unsolvable_table(r)
+    assert not u[0].any() and not u[:, 0].any()
+    for a in range(r):
+        assert u[a, a] == 0 and u[a, (r - a) % r] == 0
+    assert np.array_equal(u, u.T)
+
+
+@pytest.mark.parametrize("r", W.first_odd_primes(24))
+def test_reduced_matches_full(r):
+    """u_r(a, b) = v_r(a / b) for b != 0 (weighted homogeneity), u_r(a, 0) = 0."""
+    assert np.array_equal(O.full_from_reduced(r, O.reduced_table(r)), O.unsolvable_table(r))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("r", [r for r in W.first_odd_primes(64) if r > 97])
+def test_reduced_matches_full_to_313(r):
+    assert np.array_equal(O.full_from_reduced(r, O.reduced_table(r)), O.unsolvable_table(r))
+
+
+def test_unsolvable_counts_brute_force():
+    """Number of unsolvable k (pairs (k, 1)) for r = 11..41, by pure-Python brute force."""
+    for r in [11, 13, 17, 19, 23, 29, 31, 37, 41]:
+        brute = sum(0 if O.is_solvable(k, 1, r) else 1 for k in range(r))
+        assert O.unsolvable_count(r) == brute
+
+
+def test_effective_order_by_density():
+    primes = W.first_odd_primes(40)
+    cnt = [O.unsolvable_count(r) for r in primes]
+    order = O.effective_order(primes, cnt, True)
+    assert sorted(order) == list(range(len(primes)))
+    for a, b in zip(order, order[1:]):
+        fa, fb = cnt[a] / primes[a], cnt[b] / primes[b]
+        assert fa > fb or (fa == fb and primes[a] < primes[b])
+    assert O.effective_order(primes, cnt, False) == list(range(len(primes)))
+
+
+# ---------------------------------------------------------------- sieve and totals
+
+def _phi_sum(n):
+    phi = np.arange(n + 1, dtype=np.int64)
+    for i in range(2, n + 1):
+        if phi[i] == i:
+            phi[i::i] -= phi[i::i] // i
+    return phi
+
+
+def test_triangle_pair_count_is_totient_sum():
+    """#{1 <= q < p <= N, gcd = 1} = sum_{p=2..N} phi(p)."""
+    phi = _phi_sum(1 << 14)
+    for n in (200, 1000):
+        rng = W.triangle(n)
+        assert sum(len(O.row_pairs(p, rng)) for p in range(2, n + 1)) == int(phi[2:n + 1].sum())
+    assert int(phi[2:(1 << 14) + 1].sum()) == 81599337
+
+
+def test_pairs_vectorised_vs_pure_python():
+    g = random.Random(3)
+    for _ in range(20):
+        p_lo, q_lo = g.randint(1, 300), g.randint(1, 300)
+        rng = W.rect(p_lo, p_lo + g.randint(0, 40), q_lo, q_lo + g.randint(0, 40),
+                      q_lt_p=g.random() < 0.5, allow_diagonal=g.random() < 0.5)
+        a = [(p, int(q)) for p in range(rng["p_lo"], rng["p_hi"] + 1) for q in O.row_pairs(p, rng)]
+        assert a == list(O.pairs_in_range(rng))
+
+
+@pytest.mark.parametrize("by_density", [False, True])
+def test_sieve_vectorised_vs_pairwise(by_density):
+    """The row-vectorised sieve equals the pair-by-pair loop of section 5."""
+    primes = W.first_odd_primes(24)
+    T = O.Tables(primes, by_density)
+    for rng in [W.triangle(120), W.rect(300, 340, 1, 700), W.rect(1, 60, 1, 60, allow_diagonal=True)]:
+        a = O.sieve_range(T, rng)
+        b = O.sieve_range_pairwise(T, rng)
+        assert a == b
+        n_pairs, counts, surv = a
+        assert sum(counts) + len(surv) == n_pairs
+
+
+def test_sieve_reduced_lookup_vs_full():
+    """The reduced-table lookup path gives the same sieve as full tables."""
+    primes = W.first_odd_primes(24)
+    A = O.Tables(primes)
+    B = O.Tables(primes, full_limit=0)
+    rng = W.rect(1000, 1040, 1, 2000)
+    assert O.sieve_range(A, rng) == O.sieve_range(B, rng)
+
+
+def test_weak_sieves():
+    """With primes 3, 5, 7 (all-zero tables) every pair survives; every count is 0."""
+    rng = W.triangle(40)
+    res = O.run([3, 5, 7], [rng])["ranges"][0]
+    assert res["counts"] == [0, 0, 0]
+    assert len(res["survivors"]) == res["n_pairs"]
+    assert res["roots"] == []
+
+
+def test_sieve_soundness_on_diagonal():
+    """A pair with an integer root is never rejected: (k, k) passes every table and its
+    root k^2 is reported."""
+    primes = W.first_odd_primes(24)
+    res = O.run(primes, [W.rect(1, 50, 1, 50, allow_diagonal=True)])["ranges"][0]
+    assert [(p, q) for (p, q) in res["survivors"] if p == q] == [(k, k) for k in range(1, 51)]
+    assert res["roots"] == [(k, k, k * k) for k in range(1, 51)]
+
+
+# ---------------------------------------------------------------- roots
+
+def test_root_bound_holds():
+    """Every positive real root of R(u) = Q(sqrt u) lies below root_bound_u (numpy's
+    companion-matrix roots as the independent routine) and R(u) > 0 beyond it."""
+    g = random.Random(4)
+    for _ in range(200):
+        p, q = g.randint(1, 3000), g.randint(1, 3000)
+        c = O.q_coefficients(p, q)
+        U = O.root_bound_u(p, q)
+        roots = np.roots([float(c[k]) for k in (10, 8, 6, 4, 2, 0)])
+        pos = [z.real for z in roots if abs(z.imag) <= 1e-9 * abs(z) and z.real > 0]
+        assert all(u <= U * (1 + 1e-9) for u in pos)
+        for u in (U + 1, 2 * U, 10 * U + 7):
+            assert sum(c[2 * j] * u ** j for j in range(6)) > 0
+
+
+def test_roots_divisor_method_vs_scan():
+    """Rational-root-theorem search equals a brute-force t scan up to the root bound."""
+    for p in range(1, 9):
+        for q in range(1, 9):
+            assert O.integer_roots(p, q) == O.integer_roots_scan(p, q), (p, q)
+
+
+def test_roots_of_scaled_pairs():
+    """Roots scale with the pair: (l, l) has exactly t = l^2 (from Q_{1,1})."""
+    for lam in (1, 2, 6, 30, 210, 97 * 89):
+        assert O.integer_roots(lam, lam) == [lam * lam]
+
+
+def test_no_coprime_roots_small():
+    """Conjecture 1.1 in the small: no coprime p != q <= 24 has an integer root."""
+    for p in range(1, 25):
+        for q in range(1, 25):
+            if p != q and math.gcd(p, q) == 1:
+                assert O.integer_roots(p, q) == []
+
+
+# ---------------------------------------------------------------- section 6
+
+@pytest.mark.slow
+def test_paper_region_statistics():
+    """Section 6: no pair of the scanned region passes the 96 primes 11..541, and the
+    deepest rejecting prime is at most the 29th of the list (137).  Checked on the rows
+    152 <= p <= 200 of the segment of Eq. 5.2."""
+    primes = W.primes_between(11, 541)
+    assert len(primes) == 96 and primes[28] == 137
+    T = O.Tables(primes, full_limit=0)
+    deepest = -1
+    for rng in W.paper_region_rows(152, 200):
+        n_pairs, counts, surv = O.sieve_range(T, rng)
+        assert surv == []
+        nz = [i for i, c in enumerate(counts) if c]
+        deepest = max(deepest, max(nz))
+    assert deepest <= 28
