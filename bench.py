@@ -1,0 +1,412 @@
+"""Benchmark of the modulo-primes sieve on GB300 (one JSON line on rank 0).
+
+Workload (N=1): the triangle 1 <= q < p <= 2^14 (81,599,337 coprime pairs) with the
+first 64 odd primes, one range per launch (the plain form); synthetic, seeded inputs
+(the ranges and prime lists of the workloads module).  A step is one pass of the hot
+path over it: tile planning, the sieve with early exit and per-prime counts, survivor
+compaction and the exact root test of the survivors.  The tables (built once by the
+device table builder, timed separately) are resident inputs.  L2 is flushed (a 256 MiB
+write) before every timed step.
+
+Extra objects in the same line: the batched form against the plain form on the 4096
+rectangles of the batched workload, the large 2^20 triangle sweep, the roofline of the
+dominant kernel, the end-to-end number through the C ABI with host buffers, the oracle
+timed on the host cores, and the SM clocks sampled during the timed region.
+
+--impl reference times the oracle (the CPU restatement) on the same workload.
+Multi-GPU (torchrun): every rank runs the same workload on its own GPU (replicas, weak
+scaling); value = all ranks' pairs / max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "sieved coprime (p,q) pairs/s"
+UNIT = "pairs/s"
+OPS_PER_WORD_STEP = 10  # lane-ops of one prime test of one 32-q word (see the design notes)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched/large/e2e/cpu legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks sampler
+
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def traffic_record(kernel_src: str, workload: str):
+    """DRAM bytes per launch of the sieve kernel from a committed ncu summary, or None
+    when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "sieve_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    entry = rec.get(workload)
+    if not entry or entry.get("sieve_cu_sha256") != sha:
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+_ORACLE_TABLES = {}
+
+
+def cpu_baseline(target_s: float = 12.0, seed: int = W.DEFAULT_SEED) -> dict:
+    """The oracle as it stands, on a seeded sample of rows of the same workload."""
+    import numpy as np
+
+    import oracle as O
+    cfg = W.c2()
+    t0 = time.perf_counter()
+    if "c2" not in _ORACLE_TABLES:
+        _ORACLE_TABLES["c2"] = O.Tables(cfg["primes"], full_limit=0)
+    T = _ORACLE_TABLES["c2"]
+    build_s = time.perf_counter() - t0
+    g = W.rng(seed)
+    rows = g.permutation(np.arange(2, (1 << 14) + 1))
+    pairs = 0
+    t0 = time.perf_counter()
+    done = 0
+    for p in rows:
+        n, _, _ = O.sieve_range(T, W.rect(int(p), int(p), 1, int(p) - 1, q_lt_p=True))
+        pairs += n
+        done += 1
+        if time.perf_counter() - t0 > target_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} seeded random rows p of the 2^14 triangle ({pairs} pairs, {dt:.1f} s; "
+                      f"tables built once in {build_s:.1f} s, not timed)"}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    steps = []
+    for i in range(args.warmup):
+        cpu_baseline(target_s=1.0, seed=W.DEFAULT_SEED + 1000 + i)
+    per = min(10.0, max(2.0, 60.0 / max(args.steps, 1)))
+    for i in range(args.steps):
+        steps.append(cpu_baseline(target_s=per, seed=W.DEFAULT_SEED + i))
+    v = sum(s["value"] for s in steps) / len(steps)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": W.c2()["name"], "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": steps[-1]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    import paper_1601_00636_gb300 as cb
+
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cfg = W.c2()
+    primes = cfg["primes"]
+    rng = cfg["ranges"][0]
+    n_primes = len(primes)
+
+    # table build (timed separately, once)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t = cb.cuboid_tables_build(primes, cb.ORDER_AS_GIVEN, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    table_ms = e0.elapsed_time(e1)
+
+    res = cb.cuboid_result_create(t, 1)
+    arr = cb.ranges_array([rng])
+    dev_ranges = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to("cuda")
+
+    def step(mode=cb.MODE_PLAIN):
+        cb.cuboid_sieve_device(res, dev_ranges.data_ptr(), 1, mode, stream)
+
+    # parity of the timed configuration against the stored oracle result
+    with open(os.path.join(ROOT, "tests", "golden", "c2_as_given.json")) as f:
+        gold = json.load(f)["results"][0]
+    step()
+    cb.cuboid_result_download(res, stream)
+    assert cb.cuboid_result_wait(res) == cb.OK
+    got = cb.cuboid_result_get(res, 0, n_primes)
+    bit_exact = (got["n_pairs"] == gold["n_pairs"] and got["counts"] == gold["counts"]
+                 and [list(x) for x in got["survivors"]] == gold["survivors"]
+                 and [list(x) for x in got["roots"]] == gold["roots"])
+    n_pairs = got["n_pairs"]
+
+    # algorithmic work per launch (instrumented run, outside the timed region)
+    cb.cuboid_sieve_device(res, dev_ranges.data_ptr(), 1, cb.MODE_PLAIN | cb.MODE_COUNT_STEPS, stream)
+    cb.cuboid_result_wait(res)
+    stats = cb.cuboid_result_stats(res)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = Clocks(dev)
+    clocks.start()
+    time.sleep(0.3)
+    evs = []
+    sieve_ms, sieve_launches = 0.0, 0
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            a.record(stream)
+            step(cb.MODE_PLAIN | cb.MODE_TIME_SIEVE)
+            b.record(stream)
+        stream.synchronize()
+        ms, nl = cb.cuboid_result_sieve_ms(res) if cb.cuboid_result_wait(res) == cb.OK else (0.0, 0)
+        sieve_ms += ms
+        sieve_launches += nl
+        evs.append((a, b))
+    barrier()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t_max = torch.tensor([total_ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_s = float(t_max.item()) / 1e3
+    value = n_pairs * args.steps * world / total_s
+
+    # roofline of the dominant kernel (the sieve)
+    pk = peaks()
+    sms = cb.cuboid_device_sms()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = sms * 128 * sm_max * 1e6 / 1e12          # Tops/s: 32-bit integer lanes x clock
+    per_launch_ms = sieve_ms / max(sieve_launches, 1)
+    alg_ops = stats["word_steps"] * OPS_PER_WORD_STEP
+    achieved = alg_ops / (per_launch_ms / 1e3) / 1e12
+    traffic = traffic_record(os.path.join(ROOT, "paper_1601_00636_gb300", "csrc", "sieve.cu"), cfg["name"])
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                "frac": achieved / alu_peak, "traffic": traffic,
+                "kernel": "k_sieve", "launch_ms": per_launch_ms,
+                "peak_note": f"{sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz (sm_max_mhz of measured)",
+                "work": {"word_steps": stats["word_steps"], "words": stats["words"],
+                         "warp_steps": stats["warp_steps"], "ops_per_word_step": OPS_PER_WORD_STEP}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": cfg["name"], "pairs_per_step": n_pairs, "primes": n_primes,
+                       "form": "plain (one range per launch)", "l2": "flushed (256 MiB write) before each step",
+                       "parallelism": f"replicas x{world}"},
+            "bit_exact": bit_exact, "table_build_ms": table_ms,
+            "roofline": roofline, "clocks": clk, "gpu_launches": 4 * args.steps}
+
+    if not args.no_extras and rank == 0:
+        line["e2e"] = e2e_leg(cb, torch, primes, rng, args)
+        line["forms"] = forms_leg(cb, torch, stream, flush)
+        line["cpu_baseline"] = cpu_baseline()
+    elif rank == 0:
+        line["e2e"] = None
+
+    cb.cuboid_result_free(res)
+    cb.cuboid_tables_free(t)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e_leg(cb, torch, primes, rng, args):
+    """Through the C ABI with host buffers: the prime list and the range go host->device,
+    tables are built, the range is sieved and root-tested, and counts, survivor and root
+    records come back to the host -- all inside the timed region."""
+    s = torch.cuda.Stream()
+    k = max(3, min(args.steps, 10))
+    times = []
+    n_pairs = 0
+    for i in range(k + 2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t = cb.cuboid_tables_build(primes, 0, s)
+        res = cb.cuboid_sieve(t, rng["p_lo"], rng["p_hi"], rng["q_lo"], rng["q_hi"], cb.Q_LT_P, s)
+        cb.cuboid_result_wait(res)
+        got = cb.cuboid_result_get(res, 0, len(primes))
+        dt = time.perf_counter() - t0
+        cb.cuboid_result_free(res)
+        cb.cuboid_tables_free(t)
+        n_pairs = got["n_pairs"]
+        if i >= 2:
+            times.append(dt)
+    per = sum(times) / len(times)
+    h2d = 4 * len(primes) + 24
+    d2h = 8 * len(primes) + 8 + 128 + 4 * len(primes)
+    return {"value": n_pairs / per, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": per * 1e3, "includes": "table build + sieve + root test + result copy-back"}
+
+
+def forms_leg(cb, torch, stream, flush):
+    """Plain (one launch sequence per range) vs batched (one persistent launch from a CUDA
+    graph) on the 4096 rectangles of the batched workload, and the large 2^20 sweep."""
+    out = {}
+    c3 = W.c3()
+    t = cb.cuboid_tables_build(c3["primes"], 0, stream)
+    res = cb.cuboid_result_create(t, len(c3["ranges"]))
+    arr = cb.ranges_array(c3["ranges"])
+    dev = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to("cuda")
+    n = len(c3["ranges"])
+
+    def timed(mode, reps, np_):
+        for _ in range(2):
+            cb.cuboid_sieve_device(res, dev.data_ptr(), n, mode, stream)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                a.record(stream)
+                cb.cuboid_sieve_device(res, dev.data_ptr(), n, mode, stream)
+                b.record(stream)
+            stream.synchronize()
+            tot += a.elapsed_time(b)
+        cb.cuboid_result_download(res, stream)
+        cb.cuboid_result_wait(res)
+        pairs = sum(cb.cuboid_result_get(res, i, np_)["n_pairs"] for i in range(n))
+        return pairs, tot / reps
+
+    pairs, ms_b = timed(cb.MODE_BATCHED, 5, 128)
+    counts_b = [cb.cuboid_result_get(res, i, 128)["counts"] for i in range(0, n, 97)]
+    _, ms_p = timed(cb.MODE_PLAIN, 2, 128)
+    counts_p = [cb.cuboid_result_get(res, i, 128)["counts"] for i in range(0, n, 97)]
+    out["c3_4096_rectangles"] = {"pairs": pairs, "batched_ms": ms_b, "plain_ms": ms_p,
+                                 "batched_pairs_per_s": pairs / (ms_b / 1e3),
+                                 "plain_pairs_per_s": pairs / (ms_p / 1e3),
+                                 "batched_equals_plain": counts_b == counts_p}
+    cb.cuboid_result_free(res)
+    cb.cuboid_tables_free(t)
+
+    c4 = W.c4()
+    t = cb.cuboid_tables_build(c4["primes"], 0, stream)
+    res = cb.cuboid_result_create(t, 1)
+    arr = cb.ranges_array(c4["ranges"])
+    dev = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to("cuda")
+    n = 1
+    pairs, ms = timed(cb.MODE_BATCHED, 3, 256)
+    out["c4_triangle_2^20"] = {"pairs": pairs, "ms": ms, "pairs_per_s": pairs / (ms / 1e3)}
+    cb.cuboid_result_free(res)
+    cb.cuboid_tables_free(t)
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

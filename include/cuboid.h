@@ -1,0 +1,260 @@
+/*
+ * cuboid.h -- C ABI of libcuboid: the modulo-primes sieve for the second cuboid
+ * conjecture on one GB300 (sm_103a).
+ *
+ * Method (arXiv:1601.00636, Gallyamov, Kadyrov, Kashelevskiy, Kutlugallyamov, Sharipov):
+ *   For coprime p != q the tenth-degree polynomial Q_pq(t) of Eq. 1.1 can only have an
+ *   integer root if, for every prime r, the residue pair (p mod r, q mod r) is
+ *   "solvable" (Definition 1.1, section 2).  The unsolvability bits u_r (Eq. 2.3) of a
+ *   list of primes form a bit sieve (section 2); a pair is rejected by the first prime
+ *   of the list whose bit is 1, and the search of section 5 walks (p, q) through it.
+ *   Pairs that no prime rejects ("survivors") get an exact test for integer roots.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an int status (CUBOID_OK or a CUBOID_E* code below).
+ *     Misuse is reported by the status and never crashes (section 5 gives the same
+ *     contract for the paper's DLL).  Output arguments are written only on CUBOID_OK
+ *     unless a call says otherwise.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Calls that enqueue device work return without waiting unless they say so.
+ *   - Objects are bound to the CUDA device that was current when they were created;
+ *     use them with that device current.  The library owns every device and pinned
+ *     host buffer it allocates; handles are freed by the matching *_free/_destroy.
+ *   - Ranges are inclusive on both ends; p and q are 32-bit (1 <= p, q <= 2^32 - 1).
+ *   - Counts are indexed by the caller's prime list.  counts[i] is the number of pairs
+ *     whose FIRST rejecting prime, in the effective order, is primes[i].
+ */
+#ifndef CUBOID_H
+#define CUBOID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+/* 0, 1, 2 and 6 follow the codes of the paper's Start_searching / Release calls
+ * (section 5): 0 success, 1 busy, 2..5 out-of-range start values, 6 tables missing. */
+#define CUBOID_OK          0
+#define CUBOID_EBUSY       1  /* object in use (tables held by a server; no free slot) */
+#define CUBOID_ERANGE      2  /* a bound is 0, lo > hi, or p, q outside 32 bits */
+#define CUBOID_ENOTABLES   6  /* NULL tables handle */
+#define CUBOID_EINVAL      7  /* invalid argument (NULL pointer, bad prime list, ...) */
+#define CUBOID_ENOMEM      8  /* device or pinned allocation failed */
+#define CUBOID_ETIMEOUT    9  /* a bounded wait expired */
+#define CUBOID_ECUDA      10  /* a CUDA runtime call failed */
+#define CUBOID_EOVERFLOW  11  /* an output buffer was too small (counts stay exact) */
+#define CUBOID_EAGAIN     12  /* not finished yet (server poll) */
+#define CUBOID_EVERIFY    13  /* the exact root test could not settle a survivor */
+
+/* ------------------------------------------------------------ build flags */
+#define CUBOID_ORDER_AS_GIVEN    0x0u /* sieve the primes in the caller's order */
+#define CUBOID_ORDER_BY_DENSITY  0x1u /* decreasing unsolvable fraction, ties: smaller r */
+#define CUBOID_BUILD_REDUCED     0x0u /* u_r from v_r(k)=u_r(k,1) by homogeneity (default) */
+#define CUBOID_BUILD_FULL        0x2u /* u_r by trying every t for every (p~, q~) */
+
+/* ------------------------------------------------------------ range flags */
+#define CUBOID_Q_LT_P            0x1u /* only q < p (q <= p with ALLOW_DIAGONAL) */
+#define CUBOID_ALLOW_DIAGONAL    0x2u /* also sieve p == q, whatever gcd(p, p) (tests) */
+#define CUBOID_ROWS_P            0x4u /* force tiles with one p per row */
+#define CUBOID_ROWS_Q            0x8u /* force tiles with one q per row */
+
+/* ------------------------------------------------------------ sieve modes */
+#define CUBOID_MODE_PLAIN        0x0u /* one kernel launch sequence per range */
+#define CUBOID_MODE_BATCHED      0x1u /* all ranges in one persistent launch (CUDA graph) */
+#define CUBOID_MODE_COUNT_STEPS  0x100u /* also count sieve steps (cuboid_result_stats) */
+#define CUBOID_MODE_TIME_SIEVE   0x200u /* time the sieve kernel(s) with CUDA events */
+
+typedef struct cuboid_tables cuboid_tables;
+typedef struct cuboid_result cuboid_result;
+typedef struct cuboid_server cuboid_server;
+
+/* One rectangle [p_lo, p_hi] x [q_lo, q_hi] with CUBOID_Q_LT_P / ALLOW_DIAGONAL /
+ * ROWS_* flags; reserved must be 0.  24 bytes. */
+typedef struct cuboid_range {
+  uint32_t p_lo, p_hi, q_lo, q_hi;
+  uint32_t flags;
+  uint32_t reserved;
+} cuboid_range;
+
+/* An integer root t > 0 of Q_pq (t may exceed 64 bits: t = t_hi * 2^64 + t_lo). */
+typedef struct cuboid_root {
+  uint32_t p, q;
+  uint64_t t_lo, t_hi;
+} cuboid_root;
+
+/* Kernel shape.  Any field 0 means "library default".  Results never depend on it. */
+typedef struct cuboid_tuning {
+  uint32_t block_threads;   /* threads per CTA of the sieve kernel (multiple of 32) */
+  uint32_t ctas_per_sm;     /* persistent CTAs per SM */
+  uint32_t smem_primes;     /* how many leading primes (effective order) sit in shared memory */
+  uint32_t tiles_per_warp;  /* target number of work tiles per warp (sets the tile size) */
+} cuboid_tuning;
+
+/* Instrumentation filled by runs with CUBOID_MODE_COUNT_STEPS. */
+typedef struct cuboid_stats {
+  uint64_t words;        /* 32-q words that held at least one sieved pair */
+  uint64_t word_steps;   /* sum over words of primes tried until the word was all rejected */
+  uint64_t warp_steps;   /* prime steps executed per warp (times 32 = lane slots issued) */
+  uint64_t tiles;        /* non-empty tiles */
+} cuboid_stats;
+
+/* ================================================================ tables (section 2) */
+
+/* Build the unsolvability tables u_r (Eq. 2.3, Definition 1.1) for n primes on the
+ * current device.
+ *   primes: host array of n distinct primes, 2 <= r < 9697 (the bound below Eq. 2.7),
+ *           1 <= n <= 1024.
+ *   flags:  CUBOID_ORDER_* | CUBOID_BUILD_*.
+ *   stream: work is enqueued on it; the call synchronises the stream before returning
+ *           (the effective order is needed on the host).
+ *   out:    receives the handle; free with cuboid_tables_free.
+ * Errors: EINVAL (NULL, n out of range, r not a prime, r >= 9697, duplicates),
+ *         ENOMEM, ECUDA. */
+int cuboid_tables_build(const uint32_t* primes, uint32_t n, uint32_t flags, void* stream,
+                        cuboid_tables** out);
+
+/* Number of primes, bytes of device table memory, build flags (any pointer may be NULL). */
+int cuboid_tables_info(const cuboid_tables* t, uint32_t* n_primes, uint64_t* device_bytes,
+                       uint32_t* flags);
+
+/* The effective sieve order: order_out[k] = index (into the caller's list) of the k-th
+ * prime tried.  order_out holds n entries. */
+int cuboid_tables_order(const cuboid_tables* t, uint32_t* order_out);
+
+/* Copy the table of primes[prime_idx] in the byte layout of Eq. 2.6: bit i = p~ r + q~
+ * at byte i/8, bit position i%8 (least significant first), last byte zero-padded;
+ * ceil(r^2/8) bytes.  *written (may be NULL) receives that size.  Synchronous.
+ * Errors: EINVAL (index), EOVERFLOW (dst NULL or cap too small; *written still set). */
+int cuboid_tables_copy_bits(const cuboid_tables* t, uint32_t prime_idx, uint8_t* dst,
+                            size_t cap, size_t* written);
+
+/* Copy v_r(k) = u_r(k, 1), k = 0..r-1, one byte (0/1) per k, for primes[prime_idx].
+ * Synchronous.  Errors: EINVAL, EOVERFLOW (cap < r). */
+int cuboid_tables_copy_reduced(const cuboid_tables* t, uint32_t prime_idx, uint8_t* dst,
+                               size_t cap);
+
+/* Set / read the kernel shape used by later sieve calls on these tables. */
+int cuboid_tables_set_tuning(cuboid_tables* t, const cuboid_tuning* tune);
+int cuboid_tables_get_tuning(const cuboid_tables* t, cuboid_tuning* tune);
+
+/* Free the tables.  Returns EBUSY (and frees nothing) while a server uses them, like
+ * the paper's Release call that refuses while a search runs (section 5). */
+int cuboid_tables_free(cuboid_tables* t);
+
+/* ================================================================ sieving (sections 2, 5) */
+
+/* Allocate a reusable result object for up to max_ranges ranges, surv_cap survivor
+ * records and root_cap root records (0 = defaults 2^20 and 2^16). */
+int cuboid_result_create(const cuboid_tables* t, uint32_t max_ranges, uint64_t surv_cap,
+                         uint64_t root_cap, cuboid_result** out);
+
+/* Sieve one range: every coprime pair p != q with p_lo <= p <= p_hi, q_lo <= q <= q_hi
+ * (and the flags' restrictions) goes through the bit sieve of section 2 in the
+ * effective order; survivors get the exact integer-root test of Q_pq.  Creates *out
+ * (default capacities) and enqueues the work and the copies back on stream; call
+ * cuboid_result_wait before cuboid_result_get.  Errors: ENOTABLES, ERANGE, ENOMEM. */
+int cuboid_sieve(const cuboid_tables* t, uint32_t p_lo, uint32_t p_hi, uint32_t q_lo,
+                 uint32_t q_hi, uint32_t flags, void* stream, cuboid_result** out);
+
+/* Sieve n ranges (host array) in one persistent launch with a device work queue,
+ * replayed from a captured CUDA graph.  Creates *out with max_ranges = n. */
+int cuboid_sieve_batch(const cuboid_tables* t, const cuboid_range* ranges, uint32_t n,
+                       void* stream, cuboid_result** out);
+
+/* Reuse an existing result: copy n host ranges in (n <= max_ranges), run them with
+ * mode CUBOID_MODE_PLAIN (one launch sequence per range) or CUBOID_MODE_BATCHED (one
+ * persistent launch), optionally | CUBOID_MODE_COUNT_STEPS, and enqueue the copies
+ * back.  The previous use of res must have been waited for.  Errors: ERANGE (a bad
+ * range; nothing is launched), EINVAL. */
+int cuboid_sieve_into(cuboid_result* res, const cuboid_range* ranges, uint32_t n,
+                      uint32_t mode, void* stream);
+
+/* As cuboid_sieve_into with device-resident ranges (a device pointer to n ranges) and
+ * no copy back: results stay on the device until cuboid_result_download.  Invalid
+ * ranges are skipped on the device and reported by cuboid_result_wait as ERANGE. */
+int cuboid_sieve_device(cuboid_result* res, const cuboid_range* ranges_dev, uint32_t n,
+                        uint32_t mode, void* stream);
+
+/* Enqueue the copy of counts, pair totals and record counts to pinned host memory. */
+int cuboid_result_download(cuboid_result* res, void* stream);
+
+/* Wait for the last enqueued work of res, fetch survivor and root records and sort
+ * them.  Returns CUBOID_OK, or EOVERFLOW (a record buffer was too small: counts and
+ * pair totals are still exact), ERANGE (a device-side range was invalid) or EVERIFY. */
+int cuboid_result_wait(cuboid_result* res);
+
+/* Results of range range_idx (valid after cuboid_result_wait):
+ *   n_pairs:  coprime pairs sieved (= sum of counts + n_surv);
+ *   counts:   n_primes entries, caller order (may be NULL);
+ *   surv:     n_surv records (p << 32 | q), ascending; owned by res;
+ *   roots:    n_roots records, ascending by (p, q, t); owned by res.
+ * Any output pointer may be NULL. */
+int cuboid_result_get(const cuboid_result* res, uint32_t range_idx, uint64_t* n_pairs,
+                      uint64_t* counts, uint64_t* n_surv, const uint64_t** surv,
+                      uint64_t* n_roots, const cuboid_root** roots);
+
+/* Device time of the sieve kernel launches of the last CUBOID_MODE_TIME_SIEVE run, in
+ * milliseconds (summed over launches), and the number of those launches (after
+ * cuboid_result_wait).  EINVAL if the last run was not timed. */
+int cuboid_result_sieve_ms(const cuboid_result* res, float* ms, uint32_t* launches);
+
+/* Step counters of the last CUBOID_MODE_COUNT_STEPS run (after cuboid_result_wait). */
+int cuboid_result_stats(const cuboid_result* res, cuboid_stats* out);
+
+int cuboid_result_free(cuboid_result* res);
+
+/* ================================================================ exact root test */
+
+/* Run the exact integer-root test on n arbitrary (p, q) pairs (host arrays, p, q >= 1),
+ * whatever the sieve says.  roots_out (capacity cap) receives the roots ascending;
+ * *n_roots their number.  Synchronous on stream.  Errors: EINVAL, EOVERFLOW, EVERIFY. */
+int cuboid_verify_pairs(const uint32_t* p, const uint32_t* q, uint32_t n, void* stream,
+                        cuboid_root* roots_out, uint64_t cap, uint64_t* n_roots);
+
+/* ================================================================ serving */
+
+/* A request loop that admits range queries while others run (continuous batching):
+ * queries are admitted while slots and device memory allow, grouped by an admission
+ * thread into persistent-kernel batches on several streams, and polled by ticket.
+ *   mem_budget: device bytes the server may hold (0 = 1 GiB); max_slots: queries in
+ *   flight (0 = 4096).  The tables stay in use (cuboid_tables_free returns EBUSY) until
+ *   cuboid_server_destroy. */
+int cuboid_server_create(cuboid_tables* t, uint64_t mem_budget, uint32_t max_slots,
+                         cuboid_server** out);
+
+/* Submit one range.  *ticket identifies it.  EBUSY if no slot or memory is free right
+ * now (admission refused; retry later); ERANGE for a bad range. */
+int cuboid_server_submit(cuboid_server* s, const cuboid_range* range, uint64_t* ticket);
+
+/* Poll a ticket.  EAGAIN while running; CUBOID_OK with *out = a result holding one
+ * range (free it with cuboid_result_free); EINVAL for an unknown ticket. */
+int cuboid_server_poll(cuboid_server* s, uint64_t ticket, cuboid_result** out);
+
+/* Queue depth, queries admitted/refused/finished, batches launched (NULL-safe). */
+int cuboid_server_stats(const cuboid_server* s, uint64_t* in_flight, uint64_t* admitted,
+                        uint64_t* refused, uint64_t* finished, uint64_t* batches);
+
+/* Stop the loop (waits for work in flight, at most timeout_ms; ETIMEOUT otherwise). */
+int cuboid_server_destroy(cuboid_server* s, uint32_t timeout_ms);
+
+/* ================================================================ measurement */
+
+/* Integer-issue probe: launch `blocks` CTAs of `threads` threads, each thread running
+ * `iters` iterations of 16 independent 32-bit integer ops (kind 0: IADD3/LOP3 mix,
+ * kind 1: the sieve's lookup mix with shared-memory loads).  sink_dev: device buffer
+ * of blocks*threads uint32 (defeats dead-code elimination).  Asynchronous. */
+int cuboid_probe_int_issue(uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
+                           uint32_t* sink_dev, void* stream);
+
+/* Number of SMs of the current device and the library version string. */
+int cuboid_device_sms(uint32_t* sms);
+const char* cuboid_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUBOID_H */

@@ -1,0 +1,332 @@
+"""Python binding of libcuboid (the C ABI declared in include/cuboid.h).
+
+Argument marshalling only: every step of the sieve and of the root test runs in the
+library's CUDA kernels.  Function names are those of the C ABI.  Importing this package
+loads ``libcuboid.so`` built in-tree (``paper_1601_00636_gb300/build.py`` or
+``__graft_entry__.build()``) and raises ImportError when it is missing: there is no
+CPU fallback.
+
+Streams are passed as ``None`` (legacy default stream), an int handle, or any object
+with a ``cuda_stream`` attribute (e.g. ``torch.cuda.Stream``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcuboid.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1601_00636_gb300/build.py "
+                      "or __graft_entry__.build(); there is no CPU fallback")
+_lib = C.CDLL(LIB_PATH)
+
+# ------------------------------------------------------------------ constants (cuboid.h)
+OK, EBUSY, ERANGE, ENOTABLES, EINVAL, ENOMEM = 0, 1, 2, 6, 7, 8
+ETIMEOUT, ECUDA, EOVERFLOW, EAGAIN, EVERIFY = 9, 10, 11, 12, 13
+STATUS_NAMES = {0: "OK", 1: "EBUSY", 2: "ERANGE", 6: "ENOTABLES", 7: "EINVAL", 8: "ENOMEM",
+                9: "ETIMEOUT", 10: "ECUDA", 11: "EOVERFLOW", 12: "EAGAIN", 13: "EVERIFY"}
+
+ORDER_AS_GIVEN, ORDER_BY_DENSITY = 0x0, 0x1
+BUILD_REDUCED, BUILD_FULL = 0x0, 0x2
+Q_LT_P, ALLOW_DIAGONAL, ROWS_P, ROWS_Q = 0x1, 0x2, 0x4, 0x8
+MODE_PLAIN, MODE_BATCHED, MODE_COUNT_STEPS, MODE_TIME_SIEVE = 0x0, 0x1, 0x100, 0x200
+
+
+class CuboidError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+def _check(st: int, where: str) -> int:
+    if st != OK:
+        raise CuboidError(st, where)
+    return st
+
+
+class cuboid_range(C.Structure):
+    _fields_ = [("p_lo", C.c_uint32), ("p_hi", C.c_uint32), ("q_lo", C.c_uint32),
+                ("q_hi", C.c_uint32), ("flags", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class cuboid_root(C.Structure):
+    _fields_ = [("p", C.c_uint32), ("q", C.c_uint32), ("t_lo", C.c_uint64), ("t_hi", C.c_uint64)]
+
+
+class cuboid_tuning(C.Structure):
+    _fields_ = [("block_threads", C.c_uint32), ("ctas_per_sm", C.c_uint32),
+                ("smem_primes", C.c_uint32), ("tiles_per_warp", C.c_uint32)]
+
+
+class cuboid_stats(C.Structure):
+    _fields_ = [("words", C.c_uint64), ("word_steps", C.c_uint64), ("warp_steps", C.c_uint64),
+                ("tiles", C.c_uint64)]
+
+
+_P = C.c_void_p
+_u32, _u64 = C.c_uint32, C.c_uint64
+_SIGS = {
+    "cuboid_tables_build": (C.c_int, [C.POINTER(_u32), _u32, _u32, _P, C.POINTER(_P)]),
+    "cuboid_tables_info": (C.c_int, [_P, C.POINTER(_u32), C.POINTER(_u64), C.POINTER(_u32)]),
+    "cuboid_tables_order": (C.c_int, [_P, C.POINTER(_u32)]),
+    "cuboid_tables_copy_bits": (C.c_int, [_P, _u32, C.POINTER(C.c_uint8), C.c_size_t, C.POINTER(C.c_size_t)]),
+    "cuboid_tables_copy_reduced": (C.c_int, [_P, _u32, C.POINTER(C.c_uint8), C.c_size_t]),
+    "cuboid_tables_set_tuning": (C.c_int, [_P, C.POINTER(cuboid_tuning)]),
+    "cuboid_tables_get_tuning": (C.c_int, [_P, C.POINTER(cuboid_tuning)]),
+    "cuboid_tables_free": (C.c_int, [_P]),
+    "cuboid_result_create": (C.c_int, [_P, _u32, _u64, _u64, C.POINTER(_P)]),
+    "cuboid_sieve": (C.c_int, [_P, _u32, _u32, _u32, _u32, _u32, _P, C.POINTER(_P)]),
+    "cuboid_sieve_batch": (C.c_int, [_P, C.POINTER(cuboid_range), _u32, _P, C.POINTER(_P)]),
+    "cuboid_sieve_into": (C.c_int, [_P, C.POINTER(cuboid_range), _u32, _u32, _P]),
+    "cuboid_sieve_device": (C.c_int, [_P, _P, _u32, _u32, _P]),
+    "cuboid_result_download": (C.c_int, [_P, _P]),
+    "cuboid_result_wait": (C.c_int, [_P]),
+    "cuboid_result_get": (C.c_int, [_P, _u32, C.POINTER(_u64), C.POINTER(_u64), C.POINTER(_u64),
+                                    C.POINTER(C.POINTER(_u64)), C.POINTER(_u64),
+                                    C.POINTER(C.POINTER(cuboid_root))]),
+    "cuboid_result_sieve_ms": (C.c_int, [_P, C.POINTER(C.c_float), C.POINTER(_u32)]),
+    "cuboid_result_stats": (C.c_int, [_P, C.POINTER(cuboid_stats)]),
+    "cuboid_result_free": (C.c_int, [_P]),
+    "cuboid_verify_pairs": (C.c_int, [C.POINTER(_u32), C.POINTER(_u32), _u32, _P, C.POINTER(cuboid_root),
+                                      _u64, C.POINTER(_u64)]),
+    "cuboid_server_create": (C.c_int, [_P, _u64, _u32, C.POINTER(_P)]),
+    "cuboid_server_submit": (C.c_int, [_P, C.POINTER(cuboid_range), C.POINTER(_u64)]),
+    "cuboid_server_poll": (C.c_int, [_P, _u64, C.POINTER(_P)]),
+    "cuboid_server_stats": (C.c_int, [_P, C.POINTER(_u64), C.POINTER(_u64), C.POINTER(_u64),
+                                      C.POINTER(_u64), C.POINTER(_u64)]),
+    "cuboid_server_destroy": (C.c_int, [_P, _u32]),
+    "cuboid_probe_int_issue": (C.c_int, [_u32, _u32, _u32, _u32, _P, _P]),
+    "cuboid_device_sms": (C.c_int, [C.POINTER(_u32)]),
+    "cuboid_version": (C.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return int(getattr(s, "cuda_stream"))
+
+
+def make_range(p_lo, p_hi, q_lo, q_hi, flags=0) -> cuboid_range:
+    return cuboid_range(p_lo, p_hi, q_lo, q_hi, flags, 0)
+
+
+def range_from_dict(d: dict) -> cuboid_range:
+    """A workload range dict (workloads module) as a cuboid_range."""
+    fl = (Q_LT_P if d.get("q_lt_p") else 0) | (ALLOW_DIAGONAL if d.get("allow_diagonal") else 0)
+    fl |= int(d.get("flags", 0))
+    return make_range(d["p_lo"], d["p_hi"], d["q_lo"], d["q_hi"], fl)
+
+
+def _ranges_array(ranges):
+    arr = (cuboid_range * len(ranges))()
+    for i, r in enumerate(ranges):
+        arr[i] = r if isinstance(r, cuboid_range) else range_from_dict(r)
+    return arr
+
+
+# ------------------------------------------------------------------ tables
+
+def cuboid_tables_build(primes, flags: int = 0, stream=None) -> int:
+    n = len(primes)
+    arr = (_u32 * n)(*[int(x) for x in primes])
+    out = _P()
+    _check(_lib.cuboid_tables_build(arr, n, flags, _stream(stream), C.byref(out)), "cuboid_tables_build")
+    return out.value
+
+
+def cuboid_tables_info(t):
+    n, b, f = _u32(), _u64(), _u32()
+    _check(_lib.cuboid_tables_info(t, C.byref(n), C.byref(b), C.byref(f)), "cuboid_tables_info")
+    return n.value, b.value, f.value
+
+
+def cuboid_tables_order(t) -> list[int]:
+    n = cuboid_tables_info(t)[0]
+    arr = (_u32 * n)()
+    _check(_lib.cuboid_tables_order(t, arr), "cuboid_tables_order")
+    return list(arr)
+
+
+def cuboid_tables_copy_bits(t, prime_idx: int) -> bytes:
+    need = C.c_size_t()
+    st = _lib.cuboid_tables_copy_bits(t, prime_idx, None, 0, C.byref(need))
+    if st not in (OK, EOVERFLOW, EINVAL):
+        _check(st, "cuboid_tables_copy_bits")
+    buf = (C.c_uint8 * max(need.value, 1))()
+    _check(_lib.cuboid_tables_copy_bits(t, prime_idx, buf, need.value, C.byref(need)), "cuboid_tables_copy_bits")
+    return bytes(buf[:need.value])
+
+
+def cuboid_tables_copy_reduced(t, prime_idx: int, r: int) -> bytes:
+    buf = (C.c_uint8 * r)()
+    _check(_lib.cuboid_tables_copy_reduced(t, prime_idx, buf, r), "cuboid_tables_copy_reduced")
+    return bytes(buf)
+
+
+def cuboid_tables_set_tuning(t, block_threads=0, ctas_per_sm=0, smem_primes=0, tiles_per_warp=0):
+    tu = cuboid_tuning(block_threads, ctas_per_sm, smem_primes, tiles_per_warp)
+    _check(_lib.cuboid_tables_set_tuning(t, C.byref(tu)), "cuboid_tables_set_tuning")
+
+
+def cuboid_tables_get_tuning(t) -> dict:
+    tu = cuboid_tuning()
+    _check(_lib.cuboid_tables_get_tuning(t, C.byref(tu)), "cuboid_tables_get_tuning")
+    return {k: getattr(tu, k) for k, _ in cuboid_tuning._fields_}
+
+
+def cuboid_tables_free(t) -> int:
+    return _lib.cuboid_tables_free(t)
+
+
+# ------------------------------------------------------------------ sieving
+
+def cuboid_result_create(t, max_ranges: int, surv_cap: int = 0, root_cap: int = 0) -> int:
+    out = _P()
+    _check(_lib.cuboid_result_create(t, max_ranges, surv_cap, root_cap, C.byref(out)), "cuboid_result_create")
+    return out.value
+
+
+def cuboid_sieve(t, p_lo, p_hi, q_lo, q_hi, flags=0, stream=None) -> int:
+    out = _P()
+    _check(_lib.cuboid_sieve(t, p_lo, p_hi, q_lo, q_hi, flags, _stream(stream), C.byref(out)), "cuboid_sieve")
+    return out.value
+
+
+def cuboid_sieve_batch(t, ranges, stream=None) -> int:
+    arr = _ranges_array(ranges)
+    out = _P()
+    _check(_lib.cuboid_sieve_batch(t, arr, len(ranges), _stream(stream), C.byref(out)), "cuboid_sieve_batch")
+    return out.value
+
+
+def cuboid_sieve_into(res, ranges, mode=MODE_PLAIN, stream=None, arr=None) -> None:
+    """``arr`` may be a prebuilt ctypes array of cuboid_range (see ``ranges_array``)."""
+    arr = arr if arr is not None else _ranges_array(ranges)
+    _check(_lib.cuboid_sieve_into(res, arr, len(arr), mode, _stream(stream)), "cuboid_sieve_into")
+
+
+def ranges_array(ranges):
+    return _ranges_array(ranges)
+
+
+def cuboid_sieve_device(res, ranges_dev_ptr: int, n: int, mode=MODE_PLAIN, stream=None) -> None:
+    _check(_lib.cuboid_sieve_device(res, ranges_dev_ptr, n, mode, _stream(stream)), "cuboid_sieve_device")
+
+
+def cuboid_result_download(res, stream=None) -> None:
+    _check(_lib.cuboid_result_download(res, _stream(stream)), "cuboid_result_download")
+
+
+def cuboid_result_wait(res) -> int:
+    """Returns OK, EOVERFLOW, ERANGE or EVERIFY; raises on other errors."""
+    st = _lib.cuboid_result_wait(res)
+    if st not in (OK, EOVERFLOW, ERANGE, EVERIFY):
+        _check(st, "cuboid_result_wait")
+    return st
+
+
+def cuboid_result_get(res, range_idx: int, n_primes: int) -> dict:
+    npairs, ns, nr = _u64(), _u64(), _u64()
+    counts = (_u64 * n_primes)()
+    sp = C.POINTER(_u64)()
+    rp = C.POINTER(cuboid_root)()
+    _check(_lib.cuboid_result_get(res, range_idx, C.byref(npairs), counts, C.byref(ns), C.byref(sp),
+                                  C.byref(nr), C.byref(rp)), "cuboid_result_get")
+    surv = [(int(sp[i]) >> 32, int(sp[i]) & 0xFFFFFFFF) for i in range(ns.value)]
+    roots = [(rp[i].p, rp[i].q, (int(rp[i].t_hi) << 64) | int(rp[i].t_lo)) for i in range(nr.value)]
+    return {"n_pairs": npairs.value, "counts": list(counts), "survivors": surv, "roots": roots}
+
+
+def cuboid_result_sieve_ms(res):
+    """(milliseconds, launches) of the sieve kernels of the last timed run."""
+    ms, n = C.c_float(), _u32()
+    _check(_lib.cuboid_result_sieve_ms(res, C.byref(ms), C.byref(n)), "cuboid_result_sieve_ms")
+    return ms.value, n.value
+
+
+def cuboid_result_stats(res) -> dict:
+    s = cuboid_stats()
+    _check(_lib.cuboid_result_stats(res, C.byref(s)), "cuboid_result_stats")
+    return {k: getattr(s, k) for k, _ in cuboid_stats._fields_}
+
+
+def cuboid_result_free(res) -> int:
+    return _lib.cuboid_result_free(res)
+
+
+def cuboid_verify_pairs(ps, qs, stream=None, cap: int | None = None):
+    n = len(ps)
+    pa = (_u32 * n)(*ps)
+    qa = (_u32 * n)(*qs)
+    cap = cap if cap is not None else 5 * n + 5
+    out = (cuboid_root * cap)()
+    nr = _u64()
+    _check(_lib.cuboid_verify_pairs(pa, qa, n, _stream(stream), out, cap, C.byref(nr)), "cuboid_verify_pairs")
+    return [(out[i].p, out[i].q, (int(out[i].t_hi) << 64) | int(out[i].t_lo)) for i in range(nr.value)]
+
+
+# ------------------------------------------------------------------ serving
+
+def cuboid_server_create(t, mem_budget: int = 0, max_slots: int = 0) -> int:
+    out = _P()
+    _check(_lib.cuboid_server_create(t, mem_budget, max_slots, C.byref(out)), "cuboid_server_create")
+    return out.value
+
+
+def cuboid_server_submit(s, rng):
+    """Returns the ticket, or None when admission is refused (EBUSY)."""
+    r = rng if isinstance(rng, cuboid_range) else range_from_dict(rng)
+    tk = _u64()
+    st = _lib.cuboid_server_submit(s, C.byref(r), C.byref(tk))
+    if st == EBUSY:
+        return None
+    _check(st, "cuboid_server_submit")
+    return tk.value
+
+
+def cuboid_server_poll(s, ticket: int):
+    """Returns a result handle (one range), or None while the query runs (EAGAIN)."""
+    out = _P()
+    st = _lib.cuboid_server_poll(s, ticket, C.byref(out))
+    if st == EAGAIN:
+        return None
+    _check(st, "cuboid_server_poll")
+    return out.value
+
+
+def cuboid_server_stats(s) -> dict:
+    v = [_u64() for _ in range(5)]
+    _check(_lib.cuboid_server_stats(s, *[C.byref(x) for x in v]), "cuboid_server_stats")
+    return dict(zip(("in_flight", "admitted", "refused", "finished", "batches"), [x.value for x in v]))
+
+
+def cuboid_server_destroy(s, timeout_ms: int = 60000) -> int:
+    return _lib.cuboid_server_destroy(s, timeout_ms)
+
+
+# ------------------------------------------------------------------ measurement
+
+def cuboid_probe_int_issue(kind, blocks, threads, iters, sink_dev_ptr: int, stream=None) -> None:
+    _check(_lib.cuboid_probe_int_issue(kind, blocks, threads, iters, sink_dev_ptr, _stream(stream)),
+           "cuboid_probe_int_issue")
+
+
+def cuboid_device_sms() -> int:
+    v = _u32()
+    _check(_lib.cuboid_device_sms(C.byref(v)), "cuboid_device_sms")
+    return v.value
+
+
+def cuboid_version() -> str:
+    return _lib.cuboid_version().decode()

@@ -1,0 +1,139 @@
+// Internal declarations shared by the translation units of libcuboid.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "cuboid.h"
+
+namespace cuboid {
+
+constexpr uint32_t kMaxPrimes = 1024;
+constexpr uint32_t kPrimeLimit = 9697;     // r < 9697: the bound derived below Eq. 2.7
+constexpr uint32_t kMaxFactors = 10;       // distinct primes of a 32-bit integer <= 9
+constexpr uint32_t kRowCacheLanes = 32;    // row offsets of the first 32 primes kept per lane
+
+// Per-prime sieve constants, one entry per prime in the effective order.  16 bytes.
+struct PrimeInfo {
+  uint32_t r;      // the prime
+  uint32_t magic;  // floor(2^32 / r): residue of a 32-bit n by one mul.hi and one fix-up
+  uint32_t off;    // first word of row 0 in the window-row blob
+  uint32_t W;      // words per row: floor((r - 1) / 32) + 2
+};
+
+// Window-row layout: row a of prime r holds W 32-bit words; bit j (0 <= j < 32 W) is
+// u_r(a, j mod r).  The 32 bits u_r(a, s), ..., u_r(a, s + 31 mod r) for any s < r are
+// a funnel shift of words s/32 and s/32 + 1.
+__host__ __device__ inline uint32_t row_words(uint32_t r) { return (r - 1) / 32 + 2; }
+
+// One planned range.  32 bytes.
+struct TilePlan {
+  uint32_t x_lo, x_hi;   // row variable bounds (p, or q when kRowsQ)
+  uint32_t y_lo, y_hi;   // word-dimension bounds of the rectangle
+  uint32_t flags;        // range flags | kRowsQ
+  uint32_t chunk_words;  // words per tile (multiple of 32)
+  uint64_t tile_end;     // tiles of ranges [first, this] (inclusive prefix sum)
+};
+constexpr uint32_t kRowsQ = 0x80000000u;
+
+// Device header of a result object.
+struct DevHeader {
+  unsigned long long cursor;       // next tile of the running launch
+  unsigned long long total_tiles;  // tiles of the running launch
+  unsigned long long n_surv;       // survivors found (may exceed the capacity)
+  unsigned long long n_roots;      // roots found (may exceed the capacity)
+  unsigned long long verified_lo;  // survivors [0, verified_lo) have been root-tested
+  unsigned int status;             // kStatus* bits
+  unsigned int n_ranges;           // ranges of a batched launch (written with the ranges)
+  unsigned int verify_done;        // blocks of the running verify launch that finished
+  unsigned int pad;
+  unsigned long long stats[4];     // cuboid_stats fields
+};
+constexpr unsigned kStatusSurvOverflow = 1u;
+constexpr unsigned kStatusRootOverflow = 2u;
+constexpr unsigned kStatusBadRange = 4u;
+constexpr unsigned kStatusVerifyFail = 8u;
+
+// Odd trial-division primes below 2^16 with the exact-divisibility constants
+// inv = f^-1 mod 2^32 and lim = floor((2^32 - 1) / f):  f | n  <=>  n * inv <= lim.
+struct TrialPrime {
+  uint32_t f, inv, lim, pad;
+};
+
+}  // namespace cuboid
+
+struct cuboid_tables {
+  int device = 0;
+  uint32_t n = 0;
+  uint32_t flags = 0;
+  std::vector<uint32_t> primes;     // caller order
+  std::vector<uint32_t> order;      // effective order -> caller index
+  std::vector<uint32_t> unsolvable; // per caller index: number of k with v_r(k) = 1
+  std::vector<cuboid::PrimeInfo> info;  // effective order
+  uint64_t total_words = 0;
+  cuboid::PrimeInfo* d_info = nullptr;
+  uint32_t* d_words = nullptr;      // window rows, effective order
+  uint8_t* d_vbytes = nullptr;      // v_r bytes, caller order, at vbyte_off[i]
+  std::vector<uint64_t> vbyte_off;
+  cuboid::TrialPrime* d_trial = nullptr;
+  uint32_t n_trial = 0;
+  cuboid_tuning tuning{};
+  std::atomic<int> users{0};        // servers holding the tables
+  int sms = 0;
+};
+
+namespace cuboid {
+
+// Launch parameters of the sieve kernel.
+struct SieveArgs {
+  const PrimeInfo* info;
+  const uint32_t* words;
+  const TrialPrime* trial;
+  const TilePlan* plan;
+  DevHeader* hdr;
+  unsigned long long* counts;   // [range][prime, effective order]
+  unsigned long long* npairs;   // [range]
+  unsigned long long* surv;     // (p << 32 | q)
+  uint32_t* surv_range;
+  unsigned long long surv_cap;
+  uint32_t n_primes;
+  uint32_t n_smem_primes;
+  uint32_t smem_words;
+  uint32_t n_trial;
+  uint32_t range_first;
+  uint32_t range_count;         // UINT32_MAX: read hdr->n_ranges
+};
+
+struct VerifyArgs {
+  const unsigned long long* surv;
+  const uint32_t* surv_range;
+  unsigned long long surv_cap;
+  DevHeader* hdr;
+  cuboid_root* roots;
+  uint32_t* root_range;
+  unsigned long long root_cap;
+};
+
+// Launchers (each checks its own launch and returns cudaError_t).
+cudaError_t launch_plan(const cuboid_range* ranges, uint32_t first, uint32_t count,
+                        DevHeader* hdr, TilePlan* plan, unsigned long long* counts,
+                        unsigned long long* npairs, uint32_t n_primes, uint32_t target_tiles,
+                        cudaStream_t s);
+cudaError_t launch_reset(DevHeader* hdr, uint32_t n_ranges, cudaStream_t s);
+cudaError_t launch_sieve(const SieveArgs& a, bool count_steps, uint32_t blocks,
+                         uint32_t threads, size_t smem, cudaStream_t s);
+size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads);
+cudaError_t sieve_set_smem_limit(bool count_steps, size_t bytes);
+cudaError_t launch_verify(const VerifyArgs& a, uint32_t blocks, cudaStream_t s);
+cudaError_t verify_init_device();   // upload the 62-bit moduli (once per device)
+
+int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_t s,
+                 cuboid_tables** out);
+
+int status_from_cuda(cudaError_t e);
+
+}  // namespace cuboid

@@ -1,0 +1,652 @@
+// Host runtime of libcuboid: result objects, the plain (one range per launch) and batched
+// (one persistent launch, CUDA graph) execution paths, the exact-root-test entry point,
+// and the integer-issue probe.  The serving loop lives in server.cu.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cuboid_internal.cuh"
+
+namespace cuboid {
+
+constexpr uint64_t kDefaultSurvCap = 1ull << 20;
+constexpr uint64_t kDefaultRootCap = 1ull << 16;
+constexpr uint32_t kDefaultThreads = 512;
+constexpr uint32_t kDefaultCtasPerSm = 2;
+constexpr uint32_t kDefaultTilesPerWarp = 8;
+constexpr size_t kDefaultTableSmem = 32 * 1024;
+
+}  // namespace cuboid
+
+using namespace cuboid;
+
+struct cuboid_result {
+  const cuboid_tables* t = nullptr;
+  int device = 0;
+  uint32_t max_ranges = 0;
+  uint64_t surv_cap = 0, root_cap = 0;
+  // device
+  DevHeader* d_hdr = nullptr;
+  cuboid_range* d_ranges = nullptr;
+  TilePlan* d_plan = nullptr;
+  unsigned long long* d_counts = nullptr;
+  unsigned long long* d_npairs = nullptr;
+  unsigned long long* d_surv = nullptr;
+  uint32_t* d_surv_range = nullptr;
+  cuboid_root* d_roots = nullptr;
+  uint32_t* d_root_range = nullptr;
+  // pinned host
+  DevHeader* h_hdr = nullptr;
+  cuboid_range* h_ranges = nullptr;
+  unsigned long long* h_counts = nullptr;
+  unsigned long long* h_npairs = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph[4] = {};     // [count_steps + 2 * time_sieve]
+  cuboid_tuning graph_tuning[4] = {};  // tuning each graph was captured with
+  // last run
+  uint32_t n_ranges = 0;
+  bool downloaded = false;
+  bool fetched = false;
+  int wait_status = CUBOID_OK;
+  // host results (after wait)
+  std::vector<uint64_t> counts;  // [range][caller index]
+  std::vector<uint64_t> npairs;
+  std::vector<std::vector<uint64_t>> surv;
+  std::vector<std::vector<cuboid_root>> roots;
+  cuboid_stats stats{};
+  std::vector<cudaEvent_t> tev;  // sieve timing events, two per launch
+  uint32_t timed_launches = 0;
+  float sieve_ms = 0.f;
+  bool host_only = false;        // results delivered by the server (no device buffers)
+};
+
+namespace cuboid {
+
+struct LaunchShape {
+  uint32_t threads, blocks, n_smem, smem_words, target_tiles;
+  size_t smem;
+};
+
+static LaunchShape launch_shape(const cuboid_tables* t) {
+  const cuboid_tuning& T = t->tuning;
+  LaunchShape L;
+  L.threads = T.block_threads ? T.block_threads : kDefaultThreads;
+  const uint32_t ctas = T.ctas_per_sm ? T.ctas_per_sm : kDefaultCtasPerSm;
+  int smem_sm = 0, smem_blk = 0;
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, t->device);
+  cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, t->device);
+  const size_t fixed = sieve_smem_bytes(0, t->n, L.threads);
+  size_t per_cta = std::min<size_t>((size_t)smem_blk, (size_t)smem_sm / ctas - 1024);
+  size_t table_budget = per_cta > fixed ? per_cta - fixed : 0;
+  if (!T.smem_primes) table_budget = std::min(table_budget, kDefaultTableSmem);
+  const uint32_t want = T.smem_primes ? std::min(T.smem_primes, t->n) : t->n;
+  uint32_t k = 0;
+  uint64_t words = 0;
+  while (k < want) {
+    const PrimeInfo& pi = t->info[k];
+    const uint64_t end = (uint64_t)pi.off + (uint64_t)pi.r * pi.W;
+    if (end * 4 > table_budget) break;
+    words = end;
+    ++k;
+  }
+  L.n_smem = k;
+  L.smem_words = (uint32_t)words;
+  L.smem = sieve_smem_bytes(L.smem_words, t->n, L.threads);
+  L.blocks = (uint32_t)t->sms * ctas;
+  const uint32_t tpw = T.tiles_per_warp ? T.tiles_per_warp : kDefaultTilesPerWarp;
+  L.target_tiles = L.blocks * (L.threads / 32) * tpw;
+  return L;
+}
+
+static SieveArgs sieve_args(cuboid_result* r, const LaunchShape& L, uint32_t first, uint32_t count) {
+  const cuboid_tables* t = r->t;
+  SieveArgs a;
+  a.info = t->d_info;
+  a.words = t->d_words;
+  a.trial = t->d_trial;
+  a.plan = r->d_plan;
+  a.hdr = r->d_hdr;
+  a.counts = r->d_counts;
+  a.npairs = r->d_npairs;
+  a.surv = r->d_surv;
+  a.surv_range = r->d_surv_range;
+  a.surv_cap = r->surv_cap;
+  a.n_primes = t->n;
+  a.n_smem_primes = L.n_smem;
+  a.smem_words = L.smem_words;
+  a.n_trial = t->n_trial;
+  a.range_first = first;
+  a.range_count = count;
+  return a;
+}
+
+static VerifyArgs verify_args(cuboid_result* r) {
+  VerifyArgs v;
+  v.surv = r->d_surv;
+  v.surv_range = r->d_surv_range;
+  v.surv_cap = r->surv_cap;
+  v.hdr = r->d_hdr;
+  v.roots = r->d_roots;
+  v.root_range = r->d_root_range;
+  v.root_cap = r->root_cap;
+  return v;
+}
+
+static uint32_t verify_blocks(const cuboid_tables* t) { return (uint32_t)t->sms * 2; }
+
+// Kernels of one batched run: plan (all ranges, count read on the device), sieve, verify.
+static cudaError_t timing_events(cuboid_result* r, uint32_t launches) {
+  while (r->tev.size() < 2 * (size_t)launches) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+    r->tev.push_back(ev);
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t enqueue_batched(cuboid_result* r, const LaunchShape& L, bool steps, bool timed,
+                                   cudaStream_t s) {
+  cudaError_t e = launch_plan(r->d_ranges, 0, 0xFFFFFFFFu, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs,
+                              r->t->n, L.target_tiles, s);
+  if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[0], s);
+  if (e == cudaSuccess) e = launch_sieve(sieve_args(r, L, 0, 0xFFFFFFFFu), steps, L.blocks, L.threads, L.smem, s);
+  if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[1], s);
+  if (e == cudaSuccess) e = launch_verify(verify_args(r), verify_blocks(r->t), s);
+  return e;
+}
+
+static cudaError_t run_kernels(cuboid_result* r, uint32_t n, uint32_t mode, cudaStream_t s) {
+  const bool steps = mode & CUBOID_MODE_COUNT_STEPS;
+  const bool timed = mode & CUBOID_MODE_TIME_SIEVE;
+  const bool batched = (mode & 0xFu) == CUBOID_MODE_BATCHED;
+  const LaunchShape L = launch_shape(r->t);
+  cudaError_t e = sieve_set_smem_limit(steps, L.smem);
+  if (e != cudaSuccess) return e;
+  r->timed_launches = 0;
+  if (timed) {
+    e = timing_events(r, batched ? 1 : n);
+    if (e != cudaSuccess) return e;
+  }
+  e = launch_reset(r->d_hdr, n, s);  // zero the header, n_ranges = n
+  if (e != cudaSuccess) return e;
+  if (batched) {
+    const int gi = (steps ? 1 : 0) + (timed ? 2 : 0);
+    cudaGraphExec_t& g = r->graph[gi];
+    if (g && std::memcmp(&r->graph_tuning[gi], &r->t->tuning, sizeof(cuboid_tuning)) != 0) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+    if (timed) r->timed_launches = 1;
+    if (!g) {
+      r->graph_tuning[gi] = r->t->tuning;
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(r->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return e;
+      cudaError_t ek = enqueue_batched(r, L, steps, timed, r->cap_stream);
+      e = cudaStreamEndCapture(r->cap_stream, &graph);
+      if (ek != cudaSuccess) e = ek;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&g, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        g = nullptr;
+        return e;
+      }
+    }
+    return cudaGraphLaunch(g, s);
+  }
+  for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
+    e = launch_plan(r->d_ranges, i, 1, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs, r->t->n,
+                    L.target_tiles, s);
+    if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i], s);
+    if (e == cudaSuccess) e = launch_sieve(sieve_args(r, L, i, 1), steps, L.blocks, L.threads, L.smem, s);
+    if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i + 1], s);
+    if (e == cudaSuccess) e = launch_verify(verify_args(r), verify_blocks(r->t), s);
+  }
+  if (timed) r->timed_launches = n;
+  return e;
+}
+
+static int validate_ranges(const cuboid_range* rg, uint32_t n) {
+  for (uint32_t i = 0; i < n; ++i) {
+    const cuboid_range& R = rg[i];
+    if (R.p_lo == 0 || R.q_lo == 0 || R.p_lo > R.p_hi || R.q_lo > R.q_hi) return CUBOID_ERANGE;
+    if (R.reserved != 0 || (R.flags & ~0xFu)) return CUBOID_EINVAL;
+    if ((R.flags & CUBOID_ROWS_P) && (R.flags & CUBOID_ROWS_Q)) return CUBOID_EINVAL;
+  }
+  return CUBOID_OK;
+}
+
+static int check_device(const cuboid_result* r) {
+  int dev = -1;
+  cudaGetDevice(&dev);
+  return dev == r->device ? CUBOID_OK : CUBOID_EINVAL;
+}
+
+static void result_release(cuboid_result* r) {
+  if (!r) return;
+  if (!r->host_only) {
+    if (r->done) cudaEventSynchronize(r->done);
+    for (auto& g : r->graph)
+      if (g) cudaGraphExecDestroy(g);
+    for (auto ev : r->tev) cudaEventDestroy(ev);
+    if (r->cap_stream) cudaStreamDestroy(r->cap_stream);
+    if (r->done) cudaEventDestroy(r->done);
+    cudaFree(r->d_hdr);
+    cudaFree(r->d_ranges);
+    cudaFree(r->d_plan);
+    cudaFree(r->d_counts);
+    cudaFree(r->d_npairs);
+    cudaFree(r->d_surv);
+    cudaFree(r->d_surv_range);
+    cudaFree(r->d_roots);
+    cudaFree(r->d_root_range);
+    cudaFreeHost(r->h_hdr);
+    cudaFreeHost(r->h_ranges);
+    cudaFreeHost(r->h_counts);
+    cudaFreeHost(r->h_npairs);
+  }
+  delete r;
+}
+
+int result_create(const cuboid_tables* t, uint32_t max_ranges, uint64_t surv_cap, uint64_t root_cap,
+                  cuboid_result** out) {
+  if (!t) return CUBOID_ENOTABLES;
+  if (!out || max_ranges == 0) return CUBOID_EINVAL;
+  cuboid_result* r = new (std::nothrow) cuboid_result();
+  if (!r) return CUBOID_ENOMEM;
+  r->t = t;
+  r->device = t->device;
+  r->max_ranges = max_ranges;
+  r->surv_cap = surv_cap ? surv_cap : kDefaultSurvCap;
+  r->root_cap = root_cap ? root_cap : kDefaultRootCap;
+  const size_t nc = (size_t)max_ranges * t->n;
+  cudaError_t e = cudaSuccess;
+#define AL(call)                                      \
+  if (e == cudaSuccess) {                             \
+    e = (call);                                       \
+  }
+  AL(cudaMalloc(&r->d_hdr, sizeof(DevHeader)));
+  AL(cudaMalloc(&r->d_ranges, max_ranges * sizeof(cuboid_range)));
+  AL(cudaMalloc(&r->d_plan, max_ranges * sizeof(TilePlan)));
+  AL(cudaMalloc(&r->d_counts, nc * sizeof(unsigned long long)));
+  AL(cudaMalloc(&r->d_npairs, max_ranges * sizeof(unsigned long long)));
+  AL(cudaMalloc(&r->d_surv, r->surv_cap * sizeof(unsigned long long)));
+  AL(cudaMalloc(&r->d_surv_range, r->surv_cap * sizeof(uint32_t)));
+  AL(cudaMalloc(&r->d_roots, r->root_cap * sizeof(cuboid_root)));
+  AL(cudaMalloc(&r->d_root_range, r->root_cap * sizeof(uint32_t)));
+  AL(cudaMallocHost(&r->h_hdr, sizeof(DevHeader)));
+  AL(cudaMallocHost(&r->h_ranges, max_ranges * sizeof(cuboid_range)));
+  AL(cudaMallocHost(&r->h_counts, nc * sizeof(unsigned long long)));
+  AL(cudaMallocHost(&r->h_npairs, max_ranges * sizeof(unsigned long long)));
+  AL(cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming));
+  AL(cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking));
+  AL(cudaMemset(r->d_hdr, 0, sizeof(DevHeader)));
+#undef AL
+  if (e != cudaSuccess) {
+    result_release(r);
+    return status_from_cuda(e);
+  }
+  *out = r;
+  return CUBOID_OK;
+}
+
+static int enqueue_download(cuboid_result* r, cudaStream_t s) {
+  const size_t nc = (size_t)r->n_ranges * r->t->n;
+  cudaError_t e = cudaMemcpyAsync(r->h_hdr, r->d_hdr, sizeof(DevHeader), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && nc)
+    e = cudaMemcpyAsync(r->h_counts, r->d_counts, nc * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && r->n_ranges)
+    e = cudaMemcpyAsync(r->h_npairs, r->d_npairs, r->n_ranges * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaEventRecord(r->done, s);
+  if (e == cudaSuccess) r->downloaded = true;
+  return status_from_cuda(e);
+}
+
+int sieve_into(cuboid_result* r, const cuboid_range* ranges, uint32_t n, uint32_t mode, cudaStream_t s,
+               bool device_ranges, bool download) {
+  if (!r) return CUBOID_EINVAL;
+  if (!r->t) return CUBOID_ENOTABLES;
+  if (r->host_only || !ranges || n == 0 || n > r->max_ranges) return CUBOID_EINVAL;
+  if ((mode & ~(0xFu | CUBOID_MODE_COUNT_STEPS | CUBOID_MODE_TIME_SIEVE)) || (mode & 0xFu) > CUBOID_MODE_BATCHED)
+    return CUBOID_EINVAL;
+  if (check_device(r) != CUBOID_OK) return CUBOID_EINVAL;
+  cudaError_t e;
+  if (!device_ranges) {
+    const int st = validate_ranges(ranges, n);
+    if (st != CUBOID_OK) return st;
+    cudaEventSynchronize(r->done);  // the pinned staging may still feed an earlier copy
+    std::memcpy(r->h_ranges, ranges, n * sizeof(cuboid_range));
+    e = cudaMemcpyAsync(r->d_ranges, r->h_ranges, n * sizeof(cuboid_range), cudaMemcpyHostToDevice, s);
+  } else {
+    e = cudaMemcpyAsync(r->d_ranges, ranges, n * sizeof(cuboid_range), cudaMemcpyDeviceToDevice, s);
+  }
+  if (e != cudaSuccess) return status_from_cuda(e);
+  r->n_ranges = n;
+  r->downloaded = false;
+  r->fetched = false;
+  e = run_kernels(r, n, mode, s);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  if (download) return enqueue_download(r, s);
+  e = cudaEventRecord(r->done, s);
+  return status_from_cuda(e);
+}
+
+int result_wait(cuboid_result* r) {
+  if (!r) return CUBOID_EINVAL;
+  if (r->host_only || r->fetched) return r->wait_status;
+  if (check_device(r) != CUBOID_OK) return CUBOID_EINVAL;
+  cudaError_t e = cudaEventSynchronize(r->done);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  const cuboid_tables* t = r->t;
+  const uint32_t n = r->n_ranges;
+  const size_t nc = (size_t)n * t->n;
+  if (!r->downloaded) {
+    e = cudaMemcpy(r->h_hdr, r->d_hdr, sizeof(DevHeader), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && nc)
+      e = cudaMemcpy(r->h_counts, r->d_counts, nc * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && n)
+      e = cudaMemcpy(r->h_npairs, r->d_npairs, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return status_from_cuda(e);
+  }
+  const DevHeader H = *r->h_hdr;
+  r->counts.assign(nc, 0);
+  for (uint32_t k = 0; k < n; ++k)
+    for (uint32_t eidx = 0; eidx < t->n; ++eidx)
+      r->counts[(size_t)k * t->n + t->order[eidx]] = r->h_counts[(size_t)k * t->n + eidx];
+  r->npairs.assign(r->h_npairs, r->h_npairs + n);
+  r->surv.assign(n, {});
+  r->roots.assign(n, {});
+  const uint64_t ns = std::min<uint64_t>(H.n_surv, r->surv_cap);
+  if (ns) {
+    std::vector<unsigned long long> sv(ns);
+    std::vector<uint32_t> sr(ns);
+    e = cudaMemcpy(sv.data(), r->d_surv, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(sr.data(), r->d_surv_range, ns * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    for (uint64_t i = 0; i < ns; ++i)
+      if (sr[i] < n) r->surv[sr[i]].push_back(sv[i]);
+  }
+  const uint64_t nr = std::min<uint64_t>(H.n_roots, r->root_cap);
+  if (nr) {
+    std::vector<cuboid_root> rv(nr);
+    std::vector<uint32_t> rr(nr);
+    e = cudaMemcpy(rv.data(), r->d_roots, nr * sizeof(cuboid_root), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(rr.data(), r->d_root_range, nr * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    for (uint64_t i = 0; i < nr; ++i)
+      if (rr[i] < n) r->roots[rr[i]].push_back(rv[i]);
+  }
+  for (auto& v : r->surv) std::sort(v.begin(), v.end());
+  auto key = [](const cuboid_root& a, const cuboid_root& b) {
+    if (a.p != b.p) return a.p < b.p;
+    if (a.q != b.q) return a.q < b.q;
+    if (a.t_hi != b.t_hi) return a.t_hi < b.t_hi;
+    return a.t_lo < b.t_lo;
+  };
+  for (auto& v : r->roots) std::sort(v.begin(), v.end(), key);
+  r->sieve_ms = 0.f;
+  for (uint32_t i = 0; i < r->timed_launches; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r->tev[2 * i], r->tev[2 * i + 1]) == cudaSuccess) r->sieve_ms += ms;
+  }
+  r->stats.words = H.stats[0];
+  r->stats.word_steps = H.stats[1];
+  r->stats.warp_steps = H.stats[2];
+  r->stats.tiles = H.stats[3];
+  int st = CUBOID_OK;
+  if (H.status & kStatusVerifyFail) st = CUBOID_EVERIFY;
+  else if (H.status & kStatusBadRange) st = CUBOID_ERANGE;
+  else if (H.status & (kStatusSurvOverflow | kStatusRootOverflow)) st = CUBOID_EOVERFLOW;
+  r->wait_status = st;
+  r->fetched = true;
+  return st;
+}
+
+bool result_event_done(cuboid_result* r) { return cudaEventQuery(r->done) != cudaErrorNotReady; }
+
+cuboid_result* result_host_only(const cuboid_tables* t, uint64_t npairs, const uint64_t* counts,
+                                const uint64_t* surv, uint64_t n_surv, const cuboid_root* roots,
+                                uint64_t n_roots, int status) {
+  cuboid_result* r = new (std::nothrow) cuboid_result();
+  if (!r) return nullptr;
+  r->t = t;
+  r->device = t->device;
+  r->host_only = true;
+  r->fetched = true;
+  r->n_ranges = 1;
+  r->max_ranges = 1;
+  r->counts.assign(counts, counts + t->n);
+  r->npairs.assign(1, npairs);
+  r->surv.assign(1, std::vector<uint64_t>(surv, surv + n_surv));
+  r->roots.assign(1, std::vector<cuboid_root>(roots, roots + n_roots));
+  r->wait_status = status;
+  return r;
+}
+
+}  // namespace cuboid
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" int cuboid_result_create(const cuboid_tables* t, uint32_t max_ranges, uint64_t surv_cap,
+                                    uint64_t root_cap, cuboid_result** out) {
+  return result_create(t, max_ranges, surv_cap, root_cap, out);
+}
+
+extern "C" int cuboid_sieve(const cuboid_tables* t, uint32_t p_lo, uint32_t p_hi, uint32_t q_lo,
+                            uint32_t q_hi, uint32_t flags, void* stream, cuboid_result** out) {
+  if (!t) return CUBOID_ENOTABLES;
+  if (!out) return CUBOID_EINVAL;
+  cuboid_range R{p_lo, p_hi, q_lo, q_hi, flags, 0};
+  int st = validate_ranges(&R, 1);
+  if (st != CUBOID_OK) return st;
+  cuboid_result* r = nullptr;
+  st = result_create(t, 1, 0, 0, &r);
+  if (st != CUBOID_OK) return st;
+  st = sieve_into(r, &R, 1, CUBOID_MODE_PLAIN, (cudaStream_t)stream, false, true);
+  if (st != CUBOID_OK) {
+    result_release(r);
+    return st;
+  }
+  *out = r;
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_sieve_batch(const cuboid_tables* t, const cuboid_range* ranges, uint32_t n,
+                                  void* stream, cuboid_result** out) {
+  if (!t) return CUBOID_ENOTABLES;
+  if (!out || !ranges || n == 0) return CUBOID_EINVAL;
+  int st = validate_ranges(ranges, n);
+  if (st != CUBOID_OK) return st;
+  cuboid_result* r = nullptr;
+  st = result_create(t, n, 0, 0, &r);
+  if (st != CUBOID_OK) return st;
+  st = sieve_into(r, ranges, n, CUBOID_MODE_BATCHED, (cudaStream_t)stream, false, true);
+  if (st != CUBOID_OK) {
+    result_release(r);
+    return st;
+  }
+  *out = r;
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_sieve_into(cuboid_result* res, const cuboid_range* ranges, uint32_t n, uint32_t mode,
+                                 void* stream) {
+  return sieve_into(res, ranges, n, mode, (cudaStream_t)stream, false, true);
+}
+
+extern "C" int cuboid_sieve_device(cuboid_result* res, const cuboid_range* ranges_dev, uint32_t n,
+                                   uint32_t mode, void* stream) {
+  return sieve_into(res, ranges_dev, n, mode, (cudaStream_t)stream, true, false);
+}
+
+extern "C" int cuboid_result_download(cuboid_result* res, void* stream) {
+  if (!res || res->host_only) return CUBOID_EINVAL;
+  return enqueue_download(res, (cudaStream_t)stream);
+}
+
+extern "C" int cuboid_result_wait(cuboid_result* res) { return result_wait(res); }
+
+extern "C" int cuboid_result_get(const cuboid_result* res, uint32_t range_idx, uint64_t* n_pairs,
+                                 uint64_t* counts, uint64_t* n_surv, const uint64_t** surv,
+                                 uint64_t* n_roots, const cuboid_root** roots) {
+  if (!res || !res->fetched) return CUBOID_EINVAL;
+  if (range_idx >= res->n_ranges) return CUBOID_EINVAL;
+  const uint32_t np = res->t ? res->t->n : (uint32_t)(res->counts.size() / std::max<uint32_t>(res->n_ranges, 1));
+  if (n_pairs) *n_pairs = res->npairs[range_idx];
+  if (counts) std::memcpy(counts, res->counts.data() + (size_t)range_idx * np, np * sizeof(uint64_t));
+  if (n_surv) *n_surv = res->surv[range_idx].size();
+  if (surv) *surv = res->surv[range_idx].data();
+  if (n_roots) *n_roots = res->roots[range_idx].size();
+  if (roots) *roots = res->roots[range_idx].data();
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_result_sieve_ms(const cuboid_result* res, float* ms, uint32_t* launches) {
+  if (!res || !res->fetched || res->timed_launches == 0) return CUBOID_EINVAL;
+  if (ms) *ms = res->sieve_ms;
+  if (launches) *launches = res->timed_launches;
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_result_stats(const cuboid_result* res, cuboid_stats* out) {
+  if (!res || !out || !res->fetched) return CUBOID_EINVAL;
+  *out = res->stats;
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_result_free(cuboid_result* res) {
+  if (!res) return CUBOID_EINVAL;
+  result_release(res);
+  return CUBOID_OK;
+}
+
+// ------------------------------------------------------------------ exact root test on given pairs
+
+extern "C" int cuboid_verify_pairs(const uint32_t* p, const uint32_t* q, uint32_t n, void* stream,
+                                   cuboid_root* roots_out, uint64_t cap, uint64_t* n_roots) {
+  if (!p || !q || !n_roots || (cap && !roots_out)) return CUBOID_EINVAL;
+  for (uint32_t i = 0; i < n; ++i)
+    if (p[i] == 0 || q[i] == 0) return CUBOID_EINVAL;
+  *n_roots = 0;
+  if (n == 0) return CUBOID_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = verify_init_device();
+  if (e != cudaSuccess) return status_from_cuda(e);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t rcap = std::max<uint64_t>(cap, 5ull * n);
+  std::vector<unsigned long long> rec(n);
+  for (uint32_t i = 0; i < n; ++i) rec[i] = ((unsigned long long)p[i] << 32) | q[i];
+  DevHeader* d_hdr = nullptr;
+  unsigned long long* d_surv = nullptr;
+  cuboid_root* d_roots = nullptr;
+  uint32_t* d_rr = nullptr;
+  e = cudaMalloc(&d_hdr, sizeof(DevHeader));
+  if (e == cudaSuccess) e = cudaMalloc(&d_surv, n * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&d_roots, rcap * sizeof(cuboid_root));
+  if (e == cudaSuccess) e = cudaMalloc(&d_rr, rcap * sizeof(uint32_t));
+  DevHeader H{};
+  H.n_surv = n;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_hdr, &H, sizeof(H), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_surv, rec.data(), n * sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    VerifyArgs v;
+    v.surv = d_surv;
+    v.surv_range = nullptr;
+    v.surv_cap = n;
+    v.hdr = d_hdr;
+    v.roots = d_roots;
+    v.root_range = d_rr;
+    v.root_cap = rcap;
+    e = launch_verify(v, (uint32_t)sms * 2, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&H, d_hdr, sizeof(H), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  std::vector<cuboid_root> out;
+  if (e == cudaSuccess && H.n_roots) {
+    out.resize(std::min<uint64_t>(H.n_roots, rcap));
+    e = cudaMemcpy(out.data(), d_roots, out.size() * sizeof(cuboid_root), cudaMemcpyDeviceToHost);
+  }
+  cudaFree(d_hdr);
+  cudaFree(d_surv);
+  cudaFree(d_roots);
+  cudaFree(d_rr);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  std::sort(out.begin(), out.end(), [](const cuboid_root& a, const cuboid_root& b) {
+    if (a.p != b.p) return a.p < b.p;
+    if (a.q != b.q) return a.q < b.q;
+    if (a.t_hi != b.t_hi) return a.t_hi < b.t_hi;
+    return a.t_lo < b.t_lo;
+  });
+  *n_roots = out.size();
+  if (H.status & kStatusVerifyFail) return CUBOID_EVERIFY;
+  if (out.size() > cap) return CUBOID_EOVERFLOW;
+  if (!out.empty()) std::memcpy(roots_out, out.data(), out.size() * sizeof(cuboid_root));
+  return CUBOID_OK;
+}
+
+// ------------------------------------------------------------------ measurement helpers
+
+namespace {
+
+// kind 0: 16 independent chains of add / shift / xor (three 32-bit integer ops each).
+// kind 1: the sieve's lookup mix: shared-memory load pair, funnel shift, and, popc, xor.
+__global__ void k_probe(uint32_t kind, uint32_t iters, uint32_t* sink) {
+  __shared__ uint32_t tab[1024];
+  for (uint32_t i = threadIdx.x; i < 1024; i += blockDim.x) tab[i] = i * 2654435761u;
+  __syncthreads();
+  uint32_t a[16];
+  const uint32_t seed = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = seed * (i + 1);
+  if (kind == 0) {
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) a[i] = (a[i] + it) ^ (a[i] >> 1);
+    }
+  } else {
+    uint32_t acc = 0;
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const uint32_t wi = a[i] & 1022u;
+        const uint32_t win = __funnelshift_r(tab[wi], tab[wi + 1], a[i]);
+        acc += __popc(win & a[i]);
+        a[i] ^= win;
+      }
+    }
+    a[0] += acc;
+  }
+  uint32_t x = 0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) x ^= a[i];
+  sink[seed] = x;
+}
+
+}  // namespace
+
+extern "C" int cuboid_probe_int_issue(uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
+                                      uint32_t* sink_dev, void* stream) {
+  if (kind > 1 || blocks == 0 || threads == 0 || threads > 1024 || threads % 32 || !sink_dev)
+    return CUBOID_EINVAL;
+  k_probe<<<blocks, threads, 0, (cudaStream_t)stream>>>(kind, iters, sink_dev);
+  return status_from_cuda(cudaGetLastError());
+}
+
+extern "C" int cuboid_device_sms(uint32_t* sms) {
+  if (!sms) return CUBOID_EINVAL;
+  int dev = 0, v = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  *sms = (uint32_t)v;
+  return CUBOID_OK;
+}
+
+extern "C" const char* cuboid_version(void) { return "libcuboid 0.1 (sm_103a)"; }

@@ -1,0 +1,304 @@
+// K7: request loop with continuous batching.
+//
+// Range queries are admitted by cuboid_server_submit while a slot and memory are free
+// (admission control), queued on the host, and a dispatcher thread packs whatever is
+// pending into a batch as soon as one of several streams is free.  Each batch is one
+// persistent sieve launch (the batched path: device work queue, CUDA graph) on its own
+// stream, so batches admitted while others run overlap on the device.  Tables and the
+// per-stream result buffers stay resident; finished batches are split back into one
+// result per query, polled by ticket.  Every wait in the loop is bounded.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "cuboid_internal.cuh"
+
+struct cuboid_result;
+namespace cuboid {
+int result_create(const cuboid_tables* t, uint32_t max_ranges, uint64_t surv_cap, uint64_t root_cap,
+                  cuboid_result** out);
+int sieve_into(cuboid_result* r, const cuboid_range* ranges, uint32_t n, uint32_t mode, cudaStream_t s,
+               bool device_ranges, bool download);
+int result_wait(cuboid_result* r);
+cuboid_result* result_host_only(const cuboid_tables* t, uint64_t npairs, const uint64_t* counts,
+                                const uint64_t* surv, uint64_t n_surv, const cuboid_root* roots,
+                                uint64_t n_roots, int status);
+bool result_event_done(cuboid_result* r);
+}  // namespace cuboid
+
+using namespace cuboid;
+
+namespace {
+
+constexpr uint32_t kStreams = 4;
+constexpr uint64_t kSlotSurvCap = 1ull << 16;
+constexpr uint64_t kSlotRootCap = 1ull << 12;
+constexpr uint64_t kFreeMemMargin = 64ull << 20;
+
+struct Query {
+  uint64_t ticket;
+  cuboid_range range;
+};
+
+struct Finished {
+  uint64_t npairs = 0;
+  std::vector<uint64_t> counts;
+  std::vector<uint64_t> surv;
+  std::vector<cuboid_root> roots;
+  int status = CUBOID_OK;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cuboid_result* res = nullptr;
+  std::vector<Query> queries;
+  bool busy = false;
+};
+
+}  // namespace
+
+struct cuboid_server {
+  cuboid_tables* t = nullptr;
+  int device = 0;
+  uint64_t budget = 0;
+  uint32_t max_slots = 0;
+  uint32_t batch_cap = 0;
+  uint64_t per_query_bytes = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Query> pending;
+  std::unordered_map<uint64_t, Finished> finished;
+  std::vector<Slot> slots;
+  std::thread worker;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  uint64_t in_flight = 0, admitted = 0, refused = 0, n_finished = 0, batches = 0;
+  uint64_t free_mem = ~0ull;
+};
+
+static void collect(cuboid_server* s, Slot& sl) {
+  const int st = result_wait(sl.res);
+  const uint32_t np = s->t->n;
+  std::vector<Finished> out(sl.queries.size());
+  for (size_t k = 0; k < sl.queries.size(); ++k) {
+    Finished& f = out[k];
+    f.counts.resize(np);
+    uint64_t ns = 0, nr = 0;
+    const uint64_t* sv = nullptr;
+    const cuboid_root* rv = nullptr;
+    cuboid_result_get(sl.res, (uint32_t)k, &f.npairs, f.counts.data(), &ns, &sv, &nr, &rv);
+    f.surv.assign(sv, sv + ns);
+    f.roots.assign(rv, rv + nr);
+    f.status = st;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (size_t k = 0; k < sl.queries.size(); ++k) s->finished[sl.queries[k].ticket] = std::move(out[k]);
+  s->in_flight -= sl.queries.size();
+  s->n_finished += sl.queries.size();
+  sl.queries.clear();
+  sl.busy = false;
+}
+
+static void dispatcher(cuboid_server* s) {
+  cudaSetDevice(s->device);
+  std::vector<cuboid_range> batch;
+  auto last_mem = std::chrono::steady_clock::now();
+  for (;;) {
+    bool progressed = false;
+    for (Slot& sl : s->slots) {
+      if (sl.busy && result_event_done(sl.res)) {
+        collect(s, sl);
+        progressed = true;
+      }
+    }
+    const auto now = std::chrono::steady_clock::now();
+    if (now - last_mem > std::chrono::milliseconds(50)) {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->free_mem = fr;
+      }
+      last_mem = now;
+    }
+    for (Slot& sl : s->slots) {
+      if (sl.busy) continue;
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->pending.empty()) break;
+        while (!s->pending.empty() && sl.queries.size() < s->batch_cap) {
+          sl.queries.push_back(s->pending.front());
+          s->pending.pop_front();
+        }
+      }
+      batch.clear();
+      for (const Query& q : sl.queries) batch.push_back(q.range);
+      const int st = sieve_into(sl.res, batch.data(), (uint32_t)batch.size(), CUBOID_MODE_BATCHED, sl.stream,
+                                false, true);
+      if (st != CUBOID_OK) {  // report the failure on every query of the batch
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (const Query& q : sl.queries) {
+          Finished f;
+          f.counts.assign(s->t->n, 0);
+          f.status = st;
+          s->finished[q.ticket] = std::move(f);
+        }
+        s->in_flight -= sl.queries.size();
+        s->n_finished += sl.queries.size();
+        sl.queries.clear();
+        continue;
+      }
+      sl.busy = true;
+      progressed = true;
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->batches++;
+    }
+    std::unique_lock<std::mutex> lk(s->mu);
+    bool any_busy = false;
+    for (Slot& sl : s->slots) any_busy |= sl.busy;
+    if (s->stop && !any_busy && s->pending.empty()) break;
+    if (!progressed) {
+      if (any_busy)
+        s->cv.wait_for(lk, std::chrono::microseconds(20));
+      else
+        s->cv.wait_for(lk, std::chrono::milliseconds(2));
+    }
+  }
+}
+
+extern "C" int cuboid_server_create(cuboid_tables* t, uint64_t mem_budget, uint32_t max_slots,
+                                    cuboid_server** out) {
+  if (!t) return CUBOID_ENOTABLES;
+  if (!out) return CUBOID_EINVAL;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return CUBOID_EINVAL;
+  cuboid_server* s = new (std::nothrow) cuboid_server();
+  if (!s) return CUBOID_ENOMEM;
+  s->t = t;
+  s->device = dev;
+  s->budget = mem_budget ? mem_budget : (1ull << 30);
+  s->max_slots = max_slots ? max_slots : 4096;
+  s->batch_cap = std::max<uint32_t>(1, (s->max_slots + kStreams - 1) / kStreams);
+  // bytes one slot of a batch holds on the device (ranges, plan, counts, pair total)
+  const uint64_t per_range = sizeof(cuboid_range) + sizeof(TilePlan) + 8ull * t->n + 8;
+  const uint64_t per_batch_fixed = sizeof(DevHeader) + kSlotSurvCap * 12 + kSlotRootCap * 28;
+  const uint64_t total = kStreams * (per_batch_fixed + per_range * s->batch_cap);
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  if (total > s->budget || total + kFreeMemMargin > fr) {
+    delete s;
+    return CUBOID_ENOMEM;
+  }
+  s->per_query_bytes = per_range + per_batch_fixed / s->batch_cap;
+  s->free_mem = fr;
+  s->slots.resize(kStreams);
+  for (Slot& sl : s->slots) {
+    int st = CUBOID_OK;
+    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) st = CUBOID_ECUDA;
+    if (st == CUBOID_OK) st = result_create(t, s->batch_cap, kSlotSurvCap, kSlotRootCap, &sl.res);
+    if (st != CUBOID_OK) {
+      for (Slot& x : s->slots) {
+        if (x.res) cuboid_result_free(x.res);
+        if (x.stream) cudaStreamDestroy(x.stream);
+      }
+      delete s;
+      return st;
+    }
+  }
+  t->users++;
+  s->worker = std::thread(dispatcher, s);
+  *out = s;
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_server_submit(cuboid_server* s, const cuboid_range* range, uint64_t* ticket) {
+  if (!s || !range || !ticket) return CUBOID_EINVAL;
+  const cuboid_range& R = *range;
+  if (R.p_lo == 0 || R.q_lo == 0 || R.p_lo > R.p_hi || R.q_lo > R.q_hi) return CUBOID_ERANGE;
+  if (R.reserved || (R.flags & ~0xFu) || ((R.flags & CUBOID_ROWS_P) && (R.flags & CUBOID_ROWS_Q)))
+    return CUBOID_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) return CUBOID_EINVAL;
+  // admission: a free slot, the server's memory budget, and free device memory
+  if (s->in_flight >= s->max_slots || (s->in_flight + 1) * s->per_query_bytes > s->budget ||
+      s->free_mem < kFreeMemMargin) {
+    s->refused++;
+    return CUBOID_EBUSY;
+  }
+  const uint64_t tk = s->next_ticket++;
+  s->pending.push_back(Query{tk, R});
+  s->in_flight++;
+  s->admitted++;
+  *ticket = tk;
+  s->cv.notify_one();
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_server_poll(cuboid_server* s, uint64_t ticket, cuboid_result** out) {
+  if (!s || !out) return CUBOID_EINVAL;
+  Finished f;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->finished.find(ticket);
+    if (it == s->finished.end()) {
+      if (ticket == 0 || ticket >= s->next_ticket) return CUBOID_EINVAL;
+      bool queued = false;
+      for (const Query& q : s->pending) queued |= q.ticket == ticket;
+      for (const Slot& sl : s->slots)
+        for (const Query& q : sl.queries) queued |= q.ticket == ticket;
+      return queued ? CUBOID_EAGAIN : CUBOID_EINVAL;
+    }
+    f = std::move(it->second);
+    s->finished.erase(it);
+  }
+  cuboid_result* r = result_host_only(s->t, f.npairs, f.counts.data(), f.surv.data(), f.surv.size(),
+                                      f.roots.data(), f.roots.size(), f.status);
+  if (!r) return CUBOID_ENOMEM;
+  *out = r;
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_server_stats(const cuboid_server* s, uint64_t* in_flight, uint64_t* admitted,
+                                   uint64_t* refused, uint64_t* finished, uint64_t* batches) {
+  if (!s) return CUBOID_EINVAL;
+  cuboid_server* m = const_cast<cuboid_server*>(s);
+  std::lock_guard<std::mutex> lk(m->mu);
+  if (in_flight) *in_flight = s->in_flight;
+  if (admitted) *admitted = s->admitted;
+  if (refused) *refused = s->refused;
+  if (finished) *finished = s->n_finished;
+  if (batches) *batches = s->batches;
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_server_destroy(cuboid_server* s, uint32_t timeout_ms) {
+  if (!s) return CUBOID_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->in_flight == 0) break;
+    }
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms)) return CUBOID_ETIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  s->worker.join();
+  for (Slot& sl : s->slots) {
+    if (sl.res) cuboid_result_free(sl.res);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+  }
+  s->t->users--;
+  delete s;
+  return CUBOID_OK;
+}

@@ -1,0 +1,44 @@
+"""Writes the stored expected values of the GPU parity tests.  Calls only the oracle and
+the seeded workload generators (no GPU code).  Run from the repository root:
+
+    python tests/golden/make_golden.py
+
+Each output is JSON: {"config", "primes", "order", "ranges": [...], "results": [...]},
+one result per range: n_pairs, counts (caller order), survivors, roots.
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle as O  # noqa: E402
+import workloads as W  # noqa: E402
+
+
+def dump(name, config, primes, ranges, by_density=False):
+    t0 = time.time()
+    T = O.Tables(primes, by_density, full_limit=0)
+    res = O.run(primes, ranges, by_density, tables=T)
+    out = {"config": config, "primes": primes, "by_density": by_density, "order": res["order"],
+           "ranges": ranges, "results": res["ranges"]}
+    with open(os.path.join(HERE, name), "w") as f:
+        json.dump(out, f, separators=(",", ":"))
+    print(f"{name}: {time.time() - t0:.1f} s")
+
+
+def main():
+    c2 = W.c2()
+    dump("c2_as_given.json", c2["name"], c2["primes"], c2["ranges"])
+    dump("c2_by_density.json", c2["name"], c2["primes"], c2["ranges"], by_density=True)
+    dump("c4_rows.json", "c4 sampled rows", W.first_odd_primes(256), W.sampled_rows(1 << 20, 64))
+    rects = [r for r in W.c3()["ranges"] if (r["p_hi"] - r["p_lo"] + 1) * (r["q_hi"] - r["q_lo"] + 1) <= 1 << 16][:64]
+    dump("c3_small_rects.json", "c3 rectangles of area <= 2^16", W.first_odd_primes(128), rects)
+    c5 = W.poisson_queries(1e3, 48, log2_area=(10.0, 16.0))
+    dump("c5_small_queries.json", "c5-shaped queries of area <= 2^16", W.first_odd_primes(128), c5)
+
+
+if __name__ == "__main__":
+    main()

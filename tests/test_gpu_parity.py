@@ -1,0 +1,450 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle, bit-exact.
+
+Survivor sets, roots, per-prime counts and pair totals must equal the oracle's on the
+same seeded inputs.  Stored expected values under tests/golden/ were written by
+tests/golden/make_golden.py, which calls only the oracle.
+"""
+import json
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def cb():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1601_00636_gb300 import build as b
+    b.build()
+    import paper_1601_00636_gb300 as cb
+    torch.cuda.set_device(0)
+    return cb
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+    return torch.cuda.current_stream()
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _norm(res):
+    return {"n_pairs": res["n_pairs"], "counts": list(res["counts"]),
+            "survivors": [tuple(x) for x in res["survivors"]],
+            "roots": [tuple(x) for x in res["roots"]]}
+
+
+def _run(cb, t, n_primes, ranges, mode, stream, surv_cap=0):
+    res = cb.cuboid_result_create(t, len(ranges), surv_cap, 0)
+    try:
+        cb.cuboid_sieve_into(res, ranges, mode, stream)
+        st = cb.cuboid_result_wait(res)
+        out = [cb.cuboid_result_get(res, i, n_primes) for i in range(len(ranges))]
+    finally:
+        cb.cuboid_result_free(res)
+    return st, out
+
+
+def _check_against(got, want):
+    assert len(got) == len(want)
+    for i, (g, w) in enumerate(zip(got, want)):
+        g, w = _norm(g), _norm(w)
+        assert g["n_pairs"] == w["n_pairs"], (i, g["n_pairs"], w["n_pairs"])
+        assert g["counts"] == w["counts"], (i, g["counts"], w["counts"])
+        assert g["survivors"] == w["survivors"], i
+        assert g["roots"] == w["roots"], i
+
+
+@pytest.fixture(scope="module")
+def c1_tables(cb, stream):
+    t = cb.cuboid_tables_build(W.first_odd_primes(24), cb.ORDER_AS_GIVEN, stream)
+    yield t
+    cb.cuboid_tables_free(t)
+
+
+# ---------------------------------------------------------------- K1: tables
+
+@pytest.mark.parametrize("build", ["reduced", "full"])
+def test_c1_tables_bit_exact(cb, stream, build):
+    primes = W.first_odd_primes(24)
+    t = cb.cuboid_tables_build(primes, cb.BUILD_FULL if build == "full" else cb.BUILD_REDUCED, stream)
+    try:
+        for i, r in enumerate(primes):
+            assert cb.cuboid_tables_copy_bits(t, i) == O.pack_table_bytes(O.unsolvable_table(r)), r
+            assert np.array_equal(np.frombuffer(cb.cuboid_tables_copy_reduced(t, i, r), np.uint8),
+                                  O.reduced_table(r)), r
+    finally:
+        cb.cuboid_tables_free(t)
+
+
+def test_u11_matches_paper_through_gpu(cb, stream):
+    """Eq. 2.6 bytes of u_11 straight from the device."""
+    t = cb.cuboid_tables_build([11], 0, stream)
+    try:
+        b = cb.cuboid_tables_copy_bits(t, 0)
+    finally:
+        cb.cuboid_tables_free(t)
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "u11_bytes_eq2_6.txt")) if ln[0].isdigit()]
+    assert len(b) == 16
+    for idx, bits in rows:
+        assert format(b[int(idx)], "08b") == bits
+
+
+def _unpack(b, r):
+    bits = np.unpackbits(np.frombuffer(b, np.uint8), bitorder="little")[: r * r]
+    return bits.reshape(r, r)
+
+
+def test_full_equals_reduced_all_256_primes(cb, stream):
+    """Brute force over every t equals the homogeneity reduction, for every prime of the
+    256-prime list; each table is symmetric; every v_r equals the oracle's."""
+    primes = W.first_odd_primes(256)
+    tf = cb.cuboid_tables_build(primes, cb.BUILD_FULL, stream)
+    tr = cb.cuboid_tables_build(primes, cb.BUILD_REDUCED, stream)
+    try:
+        for i, r in enumerate(primes):
+            bf, br = cb.cuboid_tables_copy_bits(tf, i), cb.cuboid_tables_copy_bits(tr, i)
+            assert bf == br, r
+            u = _unpack(bf, r)
+            assert np.array_equal(u, u.T), r
+            assert not u[0].any() and not u[:, 0].any()
+            if i % 16 == 0 or r > 1500:
+                assert np.array_equal(np.frombuffer(cb.cuboid_tables_copy_reduced(tr, i, r), np.uint8),
+                                      O.reduced_table(r)), r
+    finally:
+        cb.cuboid_tables_free(tf)
+        cb.cuboid_tables_free(tr)
+
+
+def test_c2_primes_full_tables_vs_oracle(cb, stream):
+    primes = [r for r in W.first_odd_primes(64) if r > 97][::4]
+    t = cb.cuboid_tables_build(primes, cb.BUILD_FULL, stream)
+    try:
+        for i, r in enumerate(primes):
+            assert cb.cuboid_tables_copy_bits(t, i) == O.pack_table_bytes(O.unsolvable_table(r)), r
+    finally:
+        cb.cuboid_tables_free(t)
+
+
+@pytest.mark.parametrize("n", [24, 64, 128, 256])
+def test_effective_order(cb, stream, n):
+    primes = W.first_odd_primes(n)
+    for flag, dens in ((cb.ORDER_AS_GIVEN, False), (cb.ORDER_BY_DENSITY, True)):
+        t = cb.cuboid_tables_build(primes, flag, stream)
+        try:
+            got = cb.cuboid_tables_order(t)
+        finally:
+            cb.cuboid_tables_free(t)
+        want = O.effective_order(primes, [int(O.reduced_table(r).sum()) for r in primes], dens)
+        assert got == want
+
+
+# ---------------------------------------------------------------- K2-K4: sieve
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+@pytest.mark.parametrize("dens", [False, True])
+def test_c1_parity(cb, stream, mode, dens):
+    cfg = W.c1()
+    primes = cfg["primes"]
+    t = cb.cuboid_tables_build(primes, cb.ORDER_BY_DENSITY if dens else 0, stream)
+    try:
+        st, got = _run(cb, t, len(primes), cfg["ranges"],
+                       cb.MODE_BATCHED if mode == "batched" else cb.MODE_PLAIN, stream)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert st == cb.OK
+    want = O.run(primes, cfg["ranges"], dens)["ranges"]
+    _check_against(got, want)
+    assert got[0]["n_pairs"] == 12231
+
+
+def test_c1_north_star_call(cb, stream, c1_tables):
+    """cuboid_sieve(p_lo, p_hi, q_lo, q_hi) as the paper states the problem."""
+    res = cb.cuboid_sieve(c1_tables, 2, 200, 1, 199, cb.Q_LT_P, stream)
+    assert cb.cuboid_result_wait(res) == cb.OK
+    got = cb.cuboid_result_get(res, 0, 24)
+    cb.cuboid_result_free(res)
+    want = O.run(W.first_odd_primes(24), [W.triangle(200)])["ranges"][0]
+    _check_against([got], [want])
+
+
+@pytest.mark.parametrize("name", ["c2_as_given.json", "c2_by_density.json"])
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_c2_parity(cb, stream, name, mode):
+    g = _golden(name)
+    t = cb.cuboid_tables_build(g["primes"], cb.ORDER_BY_DENSITY if g["by_density"] else 0, stream)
+    try:
+        assert cb.cuboid_tables_order(t) == g["order"]
+        st, got = _run(cb, t, len(g["primes"]), g["ranges"],
+                       cb.MODE_BATCHED if mode == "batched" else cb.MODE_PLAIN, stream)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert st == cb.OK
+    _check_against(got, g["results"])
+    assert got[0]["n_pairs"] == 81599337
+
+
+def test_weak_sieve_every_pair_survives(cb, stream):
+    """Primes 3, 5, 7 have all-zero tables: every pair reaches the exact root test."""
+    primes = [3, 5, 7]
+    ranges = [W.triangle(80), W.rect(1, 40, 1, 40, allow_diagonal=True), W.rect(95, 130, 7, 61)]
+    t = cb.cuboid_tables_build(primes, 0, stream)
+    try:
+        for mode in (cb.MODE_PLAIN, cb.MODE_BATCHED):
+            st, got = _run(cb, t, 3, ranges, mode, stream)
+            assert st == cb.OK
+            want = O.run(primes, ranges)["ranges"]
+            _check_against(got, want)
+            assert got[1]["roots"] == [(k, k, k * k) for k in range(1, 41)]
+    finally:
+        cb.cuboid_tables_free(t)
+
+
+def test_weak_sieve_13(cb, stream):
+    primes = [13]
+    ranges = [W.triangle(150), W.rect(1, 90, 1, 90, allow_diagonal=True)]
+    t = cb.cuboid_tables_build(primes, 0, stream)
+    try:
+        st, got = _run(cb, t, 1, ranges, cb.MODE_BATCHED, stream)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert st == cb.OK
+    _check_against(got, O.run(primes, ranges)["ranges"])
+
+
+def _edge_ranges():
+    R = W.rect
+    top = (1 << 32) - 1
+    return [
+        R(5, 5, 3, 3), R(7, 7, 1, 1), R(1, 1, 1, 1, allow_diagonal=True), R(2, 2, 1, 1, q_lt_p=True),
+        R(1000, 1000, 1, 4096), R(31, 33, 30, 34), R(63, 65, 1, 200, q_lt_p=True),
+        R(1, 300, 97, 97), R(100, 101, 1, 1 << 14), R(1 << 16, (1 << 16) + 3, 1, 70000, q_lt_p=True),
+        R(top - 40, top, top - 70, top), R(top - 2, top, 1, 3000), R(4000, 4100, top - 500, top),
+        R(999983, 999983, 999000, 1000100, allow_diagonal=True),
+        R(2 * 3 * 5 * 7 * 11 * 13 * 17 * 19 * 23, 2 * 3 * 5 * 7 * 11 * 13 * 17 * 19 * 23, 1, 5000),
+        R(65521 * 65519, 65521 * 65519, 65000, 66000),
+        R(4294967294, 4294967294, 1, 3000), R(200, 260, 1, 5000, q_lt_p=True), R(1, 5000, 200, 210), R(3, 3000, 2, 3001, q_lt_p=True, allow_diagonal=True),
+    ]
+
+
+@pytest.mark.parametrize("rows", [0, "p", "q"])
+def test_edge_and_ragged_ranges(cb, stream, c1_tables, rows):
+    primes = W.first_odd_primes(24)
+    ranges = []
+    for r in _edge_ranges():
+        r = dict(r)
+        r["flags"] = {0: 0, "p": cb.ROWS_P, "q": cb.ROWS_Q}[rows]
+        ranges.append(r)
+    st, got = _run(cb, c1_tables, 24, ranges, cb.MODE_BATCHED, stream)
+    assert st == cb.OK
+    _check_against(got, O.run(primes, ranges)["ranges"])
+    st, got2 = _run(cb, c1_tables, 24, ranges, cb.MODE_PLAIN, stream)
+    assert st == cb.OK and got2 == got
+
+
+def test_transposed_rectangles(cb, stream, c1_tables):
+    """Reflection symmetry u_r(a, b) = u_r(b, a): swapping the p and q ranges transposes
+    the survivors and keeps every count."""
+    g = random.Random(7)
+    ranges, trans = [], []
+    for _ in range(40):
+        a, b = g.randint(1, 5000), g.randint(1, 5000)
+        h, w = g.randint(1, 300), g.randint(1, 300)
+        ranges.append(W.rect(a, a + h, b, b + w))
+        trans.append(W.rect(b, b + w, a, a + h))
+    st1, g1 = _run(cb, c1_tables, 24, ranges, cb.MODE_BATCHED, stream)
+    st2, g2 = _run(cb, c1_tables, 24, trans, cb.MODE_BATCHED, stream)
+    assert st1 == st2 == cb.OK
+    for x, y in zip(g1, g2):
+        assert x["counts"] == y["counts"] and x["n_pairs"] == y["n_pairs"]
+        assert sorted((q, p) for p, q in x["survivors"]) == y["survivors"]
+
+
+TUNINGS = [dict(), dict(block_threads=256, ctas_per_sm=1), dict(block_threads=1024, ctas_per_sm=1),
+           dict(smem_primes=1), dict(smem_primes=64, ctas_per_sm=1, block_threads=512),
+           dict(tiles_per_warp=1), dict(tiles_per_warp=64, ctas_per_sm=4, block_threads=128)]
+
+
+@pytest.mark.parametrize("tune", TUNINGS)
+def test_tuning_invariance_c2(cb, stream, tune):
+    g = _golden("c2_as_given.json")
+    t = cb.cuboid_tables_build(g["primes"], 0, stream)
+    try:
+        cb.cuboid_tables_set_tuning(t, **tune)
+        st, got = _run(cb, t, 64, g["ranges"], cb.MODE_BATCHED, stream)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert st == cb.OK
+    _check_against(got, g["results"])
+
+
+def test_c3_small_rectangles_vs_oracle(cb, stream):
+    g = _golden("c3_small_rects.json")
+    t = cb.cuboid_tables_build(g["primes"], 0, stream)
+    try:
+        for mode in (cb.MODE_PLAIN, cb.MODE_BATCHED):
+            st, got = _run(cb, t, 128, g["ranges"], mode, stream)
+            assert st == cb.OK
+            _check_against(got, g["results"])
+    finally:
+        cb.cuboid_tables_free(t)
+
+
+def test_c3_batched_equals_plain(cb, stream):
+    """All 4096 rectangles of the batched workload: one persistent launch gives the same
+    per-range results as 4096 separate launches."""
+    cfg = W.c3()
+    t = cb.cuboid_tables_build(cfg["primes"], 0, stream)
+    try:
+        st1, a = _run(cb, t, 128, cfg["ranges"], cb.MODE_BATCHED, stream)
+        st2, b = _run(cb, t, 128, cfg["ranges"], cb.MODE_PLAIN, stream)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert st1 == st2 == cb.OK
+    assert a == b
+    for r, x in zip(cfg["ranges"], a):
+        assert sum(x["counts"]) + len(x["survivors"]) == x["n_pairs"]
+
+
+def test_c4_sampled_rows(cb, stream):
+    g = _golden("c4_rows.json")
+    t = cb.cuboid_tables_build(g["primes"], 0, stream)
+    try:
+        st, got = _run(cb, t, 256, g["ranges"], cb.MODE_BATCHED, stream)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert st == cb.OK
+    _check_against(got, g["results"])
+
+
+def _phi_sum(n):
+    phi = np.arange(n + 1, dtype=np.int64)
+    for i in range(2, n + 1):
+        if phi[i] == i:
+            phi[i::i] -= phi[i::i] // i
+    return int(phi[2:].sum())
+
+
+def test_c4_full_triangle_totals(cb, stream):
+    """The full 1 <= q < p <= 2^20 triangle with 256 primes: pairs = sum of phi(p), every
+    pair accounted for, and the same counts under two kernel shapes."""
+    cfg = W.c4()
+    t = cb.cuboid_tables_build(cfg["primes"], 0, stream)
+    try:
+        st, a = _run(cb, t, 256, cfg["ranges"], cb.MODE_BATCHED, stream)
+        cb.cuboid_tables_set_tuning(t, block_threads=256, ctas_per_sm=4, smem_primes=40, tiles_per_warp=2)
+        st2, b = _run(cb, t, 256, cfg["ranges"], cb.MODE_PLAIN, stream)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert st == st2 == cb.OK
+    assert a == b
+    x = a[0]
+    assert x["n_pairs"] == _phi_sum(1 << 20)
+    assert sum(x["counts"]) + len(x["survivors"]) == x["n_pairs"]
+    assert x["survivors"] == []
+
+
+# ---------------------------------------------------------------- K4 on given pairs
+
+def test_verify_pairs_diagonal_and_large(cb, stream):
+    ks = list(range(1, 60)) + [1 << 20, (1 << 20) - 3, (1 << 31) + 11, (1 << 32) - 1, 4294967291]
+    got = cb.cuboid_verify_pairs(ks, ks, stream)
+    assert got == sorted((k, k, k * k) for k in ks)
+
+
+def test_verify_pairs_vs_oracle(cb, stream):
+    g = random.Random(11)
+    pairs = [(p, q) for p in range(1, 30) for q in range(1, 30)]
+    pairs += [(g.randint(1, 5000), g.randint(1, 5000)) for _ in range(300)]
+    pairs += [(l * a, l * b) for (a, b) in [(2, 3), (5, 7), (1, 4)] for l in (6, 30, 210)]
+    pairs += [(g.randint(1, (1 << 32) - 1), g.randint(1, (1 << 32) - 1)) for _ in range(4)]
+    pairs += [(1, (1 << 32) - 1), ((1 << 32) - 1, 1), (65536, 65535)]
+    got = cb.cuboid_verify_pairs([p for p, _ in pairs], [q for _, q in pairs], stream)
+    want = sorted((p, q, t) for p, q in pairs for t in O.integer_roots(p, q))
+    assert got == want
+
+
+# ---------------------------------------------------------------- contract and status codes
+
+def test_survivor_overflow_keeps_counts(cb, stream):
+    primes = [3, 5, 7]
+    t = cb.cuboid_tables_build(primes, 0, stream)
+    try:
+        st, got = _run(cb, t, 3, [W.triangle(100)], cb.MODE_BATCHED, stream, surv_cap=100)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert st == cb.EOVERFLOW
+    want = O.run(primes, [W.triangle(100)])["ranges"][0]
+    assert got[0]["n_pairs"] == want["n_pairs"] and got[0]["counts"] == want["counts"]
+
+
+def test_status_codes(cb, stream, c1_tables):
+    lib = cb._lib
+    for bad in ([4], [11, 11], [9697], [1], [], [2] * 1025):
+        with pytest.raises(cb.CuboidError) as e:
+            cb.cuboid_tables_build(bad, 0, stream)
+        assert e.value.status == cb.EINVAL
+    for args in ((0, 5, 1, 5), (5, 4, 1, 5), (1, 5, 0, 5), (1, 5, 6, 5)):
+        with pytest.raises(cb.CuboidError) as e:
+            cb.cuboid_sieve(c1_tables, *args, 0, stream)
+        assert e.value.status == cb.ERANGE
+    with pytest.raises(cb.CuboidError) as e:
+        cb.cuboid_sieve(c1_tables, 1, 5, 1, 5, cb.ROWS_P | cb.ROWS_Q, stream)
+    assert e.value.status == cb.EINVAL
+    srv = cb.cuboid_server_create(c1_tables, 0, 64)
+    try:
+        assert cb.cuboid_tables_free(c1_tables) == cb.EBUSY
+    finally:
+        assert cb.cuboid_server_destroy(srv, 10000) == cb.OK
+    assert lib.cuboid_result_get(None, 0, None, None, None, None, None, None) == cb.EINVAL
+
+
+def test_device_resident_ranges(cb, stream, c1_tables):
+    import torch
+    ranges = [W.triangle(200), W.rect(300, 400, 1, 800)]
+    arr = cb.ranges_array(ranges)
+    dev = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).cuda()
+    res = cb.cuboid_result_create(c1_tables, 2)
+    try:
+        cb.cuboid_sieve_device(res, dev.data_ptr(), 2, cb.MODE_BATCHED, stream)
+        cb.cuboid_result_download(res, stream)
+        assert cb.cuboid_result_wait(res) == cb.OK
+        got = [cb.cuboid_result_get(res, i, 24) for i in range(2)]
+    finally:
+        cb.cuboid_result_free(res)
+    _check_against(got, O.run(W.first_odd_primes(24), ranges)["ranges"])
+
+
+def test_count_steps_instrumentation(cb, stream, c1_tables):
+    rng = [W.triangle(2000)]
+    res = cb.cuboid_result_create(c1_tables, 1)
+    try:
+        cb.cuboid_sieve_into(res, rng, cb.MODE_BATCHED | cb.MODE_COUNT_STEPS, stream)
+        assert cb.cuboid_result_wait(res) == cb.OK
+        got = cb.cuboid_result_get(res, 0, 24)
+        s = cb.cuboid_result_stats(res)
+    finally:
+        cb.cuboid_result_free(res)
+    _check_against([got], O.run(W.first_odd_primes(24), rng)["ranges"])
+    assert s["words"] > 0 and s["tiles"] > 0
+    assert s["words"] <= s["word_steps"] <= 32 * s["warp_steps"]
+
+
+def test_repeat_is_deterministic(cb, stream, c1_tables):
+    rng = [W.rect(1, 3000, 1, 3000, q_lt_p=True), W.rect(5000, 6000, 1, 20)]
+    a = _run(cb, c1_tables, 24, rng, cb.MODE_BATCHED, stream)
+    b = _run(cb, c1_tables, 24, rng, cb.MODE_BATCHED, stream)
+    assert a == b
