@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -10,7 +11,7 @@ from concurrent.futures import ThreadPoolExecutor
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-BUILD = os.path.join(PKG, "_build")
+BUILD = os.path.join(PKG, "_build", platform.machine())
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libcuboid.so")
 SOURCES = ["tables.cu", "sieve.cu", "verify.cu", "runtime.cu", "server.cu"]
@@ -37,6 +38,17 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 
+def _arch_of(path: str) -> str:
+    """Machine of an ELF shared object (x86_64 / aarch64), from its header."""
+    try:
+        with open(path, "rb") as f:
+            head = f.read(20)
+    except OSError:
+        return ""
+    mach = int.from_bytes(head[18:20], "little")
+    return {62: "x86_64", 183: "aarch64"}.get(mach, str(mach))
+
+
 def build(verbose: bool = False, ptxas_verbose: bool = False, force: bool = False) -> str:
     """Compile every source and link libcuboid.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
@@ -53,7 +65,7 @@ def build(verbose: bool = False, ptxas_verbose: bool = False, force: bool = Fals
         p = subprocess.run(cmd, capture_output=True, text=True)
         return cmd, p
 
-    relink = bool(jobs) or not os.path.exists(LIB)
+    relink = bool(jobs) or not os.path.exists(LIB) or _arch_of(LIB) != platform.machine()
     with ThreadPoolExecutor(max_workers=min(8, max(1, len(jobs)))) as ex:
         for cmd, p in ex.map(run, jobs):
             if verbose or ptxas_verbose or p.returncode:

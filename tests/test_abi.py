@@ -23,8 +23,8 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def lib_path():
-    from paper_1601_00636_gb300 import build as b
-    return b.build()
+    import __graft_entry__
+    return __graft_entry__._builder().build()
 
 
 def test_header_declares_functions():

@@ -23,8 +23,8 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 def cb():
     import torch
     assert torch.cuda.is_available(), "GPU tests need CUDA"
-    from paper_1601_00636_gb300 import build as b
-    b.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1601_00636_gb300 as cb
     torch.cuda.set_device(0)
     return cb
