@@ -289,15 +289,16 @@ def _factor(n: int) -> dict[int, int]:
 
 
 def _ceil_root(x: int, k: int) -> int:
-    """Smallest integer y >= 0 with y^k >= x."""
+    """Smallest integer y >= 0 with y^k >= x (exact integer Newton iteration)."""
     if x <= 0:
         return 0
-    y = int(round(x ** (1.0 / k))) if x < 1 << 1000 else 1 << (x.bit_length() // k + 1)
-    while y ** k < x:
-        y += 1
-    while y > 0 and (y - 1) ** k >= x:
-        y -= 1
-    return y
+    y = 1 << ((x.bit_length() + k - 1) // k)       # y^k >= x
+    while True:
+        z = ((k - 1) * y + x // y ** (k - 1)) // k
+        if z >= y:
+            break
+        y = z                                        # y = floor(x^(1/k)) on exit
+    return y if y ** k >= x else y + 1
 
 
 def root_bound_u(p: int, q: int) -> int:

@@ -328,3 +328,17 @@ def test_paper_region_statistics():
         nz = [i for i, c in enumerate(counts) if c]
         deepest = max(deepest, max(nz))
     assert deepest <= 28
+
+
+def test_ceil_root_exact():
+    """The integer k-th root used by the root bound is exact on huge integers."""
+    from oracle.cuboid_oracle import _ceil_root
+    g = random.Random(5)
+    for _ in range(3000):
+        x = g.randint(1, 10 ** g.randint(1, 250))
+        k = g.randint(1, 5)
+        y = _ceil_root(x, k)
+        assert y ** k >= x and (y - 1) ** k < x
+    for k in (2, 3, 5):
+        for b in (1, 2, 10 ** 40 + 1):
+            assert _ceil_root(b ** k, k) == b
