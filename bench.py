@@ -138,6 +138,28 @@ def traffic_record(kernel_src: str, workload: str):
 _ORACLE_TABLES = {}
 
 
+def int_issue_probe(cb, torch, stream):
+    """Measured 32-bit integer issue rate (lane-ops/s) of a dependency-free add/shift/xor
+    stream on every SM, and the rate of the sieve's lookup mix (shared-memory load pair,
+    funnel shift, and, popc, xor)."""
+    sms = cb.cuboid_device_sms()
+    blocks, threads, iters = sms * 8, 256, 4096
+    sink = torch.empty(blocks * threads, dtype=torch.int32, device="cuda")
+    out = {}
+    for kind, ops in ((0, 48), (1, 16 * 6)):
+        for _ in range(2):
+            cb.cuboid_probe_int_issue(kind, blocks, threads, iters, sink.data_ptr(), stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            cb.cuboid_probe_int_issue(kind, blocks, threads, iters, sink.data_ptr(), stream)
+            b.record(stream)
+        stream.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        out["alu_tops" if kind == 0 else "lookup_mix_tops"] = blocks * threads * iters * ops / sec / 1e12
+    return out
+
+
 def cpu_baseline(target_s: float = 12.0, seed: int = W.DEFAULT_SEED) -> dict:
     """The oracle as it stands, on a seeded sample of rows of the same workload."""
     import numpy as np
@@ -286,8 +308,9 @@ def run_ours(args):
     alg_ops = stats["word_steps"] * OPS_PER_WORD_STEP
     achieved = alg_ops / (per_launch_ms / 1e3) / 1e12
     traffic = traffic_record(os.path.join(ROOT, "paper_1601_00636_gb300", "csrc", "sieve.cu"), cfg["name"])
+    probe = int_issue_probe(cb, torch, stream)
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "traffic": traffic,
+                "frac": achieved / alu_peak, "traffic": traffic, "probe": probe,
                 "kernel": "k_sieve", "launch_ms": per_launch_ms,
                 "peak_note": f"{sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz (sm_max_mhz of measured)",
                 "work": {"word_steps": stats["word_steps"], "words": stats["words"],
