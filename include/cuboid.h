@@ -48,6 +48,7 @@ extern "C" {
 #define CUBOID_EOVERFLOW  11  /* an output buffer was too small (counts stay exact) */
 #define CUBOID_EAGAIN     12  /* not finished yet (server poll) */
 #define CUBOID_EVERIFY    13  /* the exact root test could not settle a survivor */
+#define CUBOID_ETOOLARGE  14  /* more ranges than the fixed capacity of cuboid_sieve_noalloc */
 
 /* ------------------------------------------------------------ build flags */
 #define CUBOID_ORDER_AS_GIVEN    0x0u /* sieve the primes in the caller's order */
@@ -205,6 +206,45 @@ int cuboid_result_sieve_ms(const cuboid_result* res, float* ms, uint32_t* launch
 int cuboid_result_stats(const cuboid_result* res, cuboid_stats* out);
 
 int cuboid_result_free(cuboid_result* res);
+
+/* ================================================================ no-allocation sieve */
+
+/* Largest number of ranges one cuboid_sieve_noalloc call accepts. */
+#define CUBOID_NOALLOC_MAX_RANGES 4096
+
+/* The batched sieve (all n ranges in one persistent launch, then the exact root test of
+ * the survivors) for callers that may not allocate device memory when they sieve: a
+ * loop with a latency budget (cudaMalloc and cudaFree synchronise the device), code
+ * that records work into a CUDA graph, a host that only lends the library a fixed pool,
+ * or a process at its memory limit.  This call allocates nothing and calls no
+ * allocating routine.  Its working memory (tile plans and the tile-queue/counter header,
+ * 4096 x 32 bytes + 256 bytes) is one static array of device memory that every GPU that
+ * loads the library holds until the process exits.  No paper counterpart: the paper
+ * runs one CPU thread with host memory.
+ *
+ *   t:              tables built beforehand (cuboid_tables_build allocates; do it at set-up).
+ *   ranges_dev:     device pointer to n ranges, 1 <= n <= CUBOID_NOALLOC_MAX_RANGES.
+ *   counts_dev:     device, n * n_primes uint64, written (zeroed first); counts_dev[k * n_primes + e]
+ *                   is the count of the e-th prime of the EFFECTIVE order (cuboid_tables_order).
+ *   npairs_dev:     device, n uint64: pairs sieved per range.
+ *   surv_dev, surv_range_dev, surv_cap: device survivor records (p << 32 | q, unsorted) and
+ *                   their range index; records beyond surv_cap are dropped (counts stay exact).
+ *   roots_dev, root_range_dev, root_cap: device root records (unsorted) and range indices.
+ *   totals_dev:     device, 3 uint64: number of survivors, number of roots (both may exceed
+ *                   the capacities), and the device status bits (0 = clean; 1 survivor
+ *                   overflow, 2 root overflow, 4 invalid range, 8 root test unsettled).
+ *   stream:         everything is enqueued on it; the call returns without waiting.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents (each call clears what must start at zero), so calls
+ * whose work overlaps on the GPU (other streams, other host threads) race: serialise them.
+ * Errors: ENOTABLES, ETOOLARGE (n > CUBOID_NOALLOC_MAX_RANGES, nothing enqueued), EINVAL,
+ * ECUDA. */
+int cuboid_sieve_noalloc(const cuboid_tables* t, const cuboid_range* ranges_dev, uint32_t n,
+                         uint64_t* counts_dev, uint64_t* npairs_dev, uint64_t* surv_dev,
+                         uint32_t* surv_range_dev, uint64_t surv_cap, cuboid_root* roots_dev,
+                         uint32_t* root_range_dev, uint64_t root_cap, uint64_t* totals_dev,
+                         void* stream);
 
 /* ================================================================ exact root test */
 

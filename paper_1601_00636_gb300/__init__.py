@@ -24,9 +24,10 @@ _lib = C.CDLL(LIB_PATH)
 
 # ------------------------------------------------------------------ constants (cuboid.h)
 OK, EBUSY, ERANGE, ENOTABLES, EINVAL, ENOMEM = 0, 1, 2, 6, 7, 8
-ETIMEOUT, ECUDA, EOVERFLOW, EAGAIN, EVERIFY = 9, 10, 11, 12, 13
+ETIMEOUT, ECUDA, EOVERFLOW, EAGAIN, EVERIFY, ETOOLARGE = 9, 10, 11, 12, 13, 14
+NOALLOC_MAX_RANGES = 4096
 STATUS_NAMES = {0: "OK", 1: "EBUSY", 2: "ERANGE", 6: "ENOTABLES", 7: "EINVAL", 8: "ENOMEM",
-                9: "ETIMEOUT", 10: "ECUDA", 11: "EOVERFLOW", 12: "EAGAIN", 13: "EVERIFY"}
+                9: "ETIMEOUT", 10: "ECUDA", 11: "EOVERFLOW", 12: "EAGAIN", 13: "EVERIFY", 14: "ETOOLARGE"}
 
 ORDER_AS_GIVEN, ORDER_BY_DENSITY = 0x0, 0x1
 BUILD_REDUCED, BUILD_FULL = 0x0, 0x2
@@ -89,6 +90,7 @@ _SIGS = {
     "cuboid_result_sieve_ms": (C.c_int, [_P, C.POINTER(C.c_float), C.POINTER(_u32)]),
     "cuboid_result_stats": (C.c_int, [_P, C.POINTER(cuboid_stats)]),
     "cuboid_result_free": (C.c_int, [_P]),
+    "cuboid_sieve_noalloc": (C.c_int, [_P, _P, _u32, _P, _P, _P, _P, _u64, _P, _P, _u64, _P, _P]),
     "cuboid_verify_pairs": (C.c_int, [C.POINTER(_u32), C.POINTER(_u32), _u32, _P, C.POINTER(cuboid_root),
                                       _u64, C.POINTER(_u64)]),
     "cuboid_server_create": (C.c_int, [_P, _u64, _u32, C.POINTER(_P)]),
@@ -263,6 +265,16 @@ def cuboid_result_stats(res) -> dict:
 
 def cuboid_result_free(res) -> int:
     return _lib.cuboid_result_free(res)
+
+
+def cuboid_sieve_noalloc(t, ranges_dev_ptr: int, n: int, counts_dev_ptr: int, npairs_dev_ptr: int,
+                         surv_dev_ptr: int, surv_range_dev_ptr: int, surv_cap: int, roots_dev_ptr: int,
+                         root_range_dev_ptr: int, root_cap: int, totals_dev_ptr: int, stream=None) -> int:
+    """The allocation-free sieve: every buffer is a device pointer owned by the caller.
+    Returns the status code (ETOOLARGE for too many ranges) instead of raising."""
+    return _lib.cuboid_sieve_noalloc(t, ranges_dev_ptr, n, counts_dev_ptr, npairs_dev_ptr, surv_dev_ptr,
+                                     surv_range_dev_ptr, surv_cap, roots_dev_ptr, root_range_dev_ptr,
+                                     root_cap, totals_dev_ptr, _stream(stream))
 
 
 def cuboid_verify_pairs(ps, qs, stream=None, cap: int | None = None):

@@ -131,6 +131,13 @@ cudaError_t sieve_set_smem_limit(bool count_steps, size_t bytes);
 cudaError_t launch_verify(const VerifyArgs& a, uint32_t blocks, cudaStream_t s);
 cudaError_t verify_init_device();   // upload the 62-bit moduli (once per device)
 
+// Sieve launch shape chosen from the tables' tuning (runtime.cu).
+struct LaunchShape {
+  uint32_t threads, blocks, n_smem, smem_words, target_tiles;
+  size_t smem;
+};
+LaunchShape launch_shape(const cuboid_tables* t);
+
 int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_t s,
                  cuboid_tables** out);
 

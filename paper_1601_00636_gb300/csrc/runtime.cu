@@ -64,12 +64,7 @@ struct cuboid_result {
 
 namespace cuboid {
 
-struct LaunchShape {
-  uint32_t threads, blocks, n_smem, smem_words, target_tiles;
-  size_t smem;
-};
-
-static LaunchShape launch_shape(const cuboid_tables* t) {
+LaunchShape launch_shape(const cuboid_tables* t) {
   const cuboid_tuning& T = t->tuning;
   LaunchShape L;
   L.threads = T.block_threads ? T.block_threads : kDefaultThreads;
