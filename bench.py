@@ -241,7 +241,7 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        t = cb.cuboid_tables_build(primes, cb.ORDER_AS_GIVEN, stream)
+        t = cb.cuboid_tables_build(primes, cb.ORDER_BY_RATE, stream)
         e1.record(stream)
     torch.cuda.synchronize()
     table_ms = e0.elapsed_time(e1)
@@ -254,7 +254,7 @@ def run_ours(args):
         cb.cuboid_sieve_device(res, dev_ranges.data_ptr(), 1, mode, stream)
 
     # parity of the timed configuration against the stored oracle result
-    with open(os.path.join(ROOT, "tests", "golden", "c2_as_given.json")) as f:
+    with open(os.path.join(ROOT, "tests", "golden", "c2_by_rate.json")) as f:
         gold = json.load(f)["results"][0]
     step()
     cb.cuboid_result_download(res, stream)
@@ -320,6 +320,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": cfg["name"], "pairs_per_step": n_pairs, "primes": n_primes,
+                       "order": "rejection rate (CUBOID_ORDER_BY_RATE)",
                        "form": "plain (one range per launch)", "l2": "flushed (256 MiB write) before each step",
                        "parallelism": f"replicas x{world}"},
             "bit_exact": bit_exact, "table_build_ms": table_ms,
@@ -352,7 +353,7 @@ def e2e_leg(cb, torch, primes, rng, args):
     for i in range(k + 2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        t = cb.cuboid_tables_build(primes, 0, s)
+        t = cb.cuboid_tables_build(primes, cb.ORDER_BY_RATE, s)
         res = cb.cuboid_sieve(t, rng["p_lo"], rng["p_hi"], rng["q_lo"], rng["q_hi"], cb.Q_LT_P, s)
         cb.cuboid_result_wait(res)
         got = cb.cuboid_result_get(res, 0, len(primes))
@@ -374,7 +375,7 @@ def forms_leg(cb, torch, stream, flush):
     graph) on the 4096 rectangles of the batched workload, and the large 2^20 sweep."""
     out = {}
     c3 = W.c3()
-    t = cb.cuboid_tables_build(c3["primes"], 0, stream)
+    t = cb.cuboid_tables_build(c3["primes"], cb.ORDER_BY_RATE, stream)
     res = cb.cuboid_result_create(t, len(c3["ranges"]))
     arr = cb.ranges_array(c3["ranges"])
     dev = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to("cuda")
@@ -411,7 +412,7 @@ def forms_leg(cb, torch, stream, flush):
     cb.cuboid_tables_free(t)
 
     c4 = W.c4()
-    t = cb.cuboid_tables_build(c4["primes"], 0, stream)
+    t = cb.cuboid_tables_build(c4["primes"], cb.ORDER_BY_RATE, stream)
     res = cb.cuboid_result_create(t, 1)
     arr = cb.ranges_array(c4["ranges"])
     dev = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to("cuda")

@@ -53,6 +53,8 @@ extern "C" {
 /* ------------------------------------------------------------ build flags */
 #define CUBOID_ORDER_AS_GIVEN    0x0u /* sieve the primes in the caller's order */
 #define CUBOID_ORDER_BY_DENSITY  0x1u /* decreasing unsolvable fraction, ties: smaller r */
+#define CUBOID_ORDER_BY_RATE     0x4u /* decreasing rejection rate of a coprime pair: the
+                                         number of unsolvable k over r + 1; ties: smaller r */
 #define CUBOID_BUILD_REDUCED     0x0u /* u_r from v_r(k)=u_r(k,1) by homogeneity (default) */
 #define CUBOID_BUILD_FULL        0x2u /* u_r by trying every t for every (p~, q~) */
 
@@ -92,6 +94,8 @@ typedef struct cuboid_tuning {
   uint32_t ctas_per_sm;     /* persistent CTAs per SM */
   uint32_t smem_primes;     /* how many leading primes (effective order) sit in shared memory */
   uint32_t tiles_per_warp;  /* target number of work tiles per warp (sets the tile size) */
+  uint32_t hot_primes;      /* leading primes tested without an early-exit check (0, 2, 4, 6) */
+  uint32_t reserved;        /* must be 0 */
 } cuboid_tuning;
 
 /* Instrumentation filled by runs with CUBOID_MODE_COUNT_STEPS. */
@@ -108,7 +112,7 @@ typedef struct cuboid_stats {
  * current device.
  *   primes: host array of n distinct primes, 2 <= r < 9697 (the bound below Eq. 2.7),
  *           1 <= n <= 1024.
- *   flags:  CUBOID_ORDER_* | CUBOID_BUILD_*.
+ *   flags:  one CUBOID_ORDER_* | CUBOID_BUILD_*.
  *   stream: work is enqueued on it; the call synchronises the stream before returning
  *           (the effective order is needed on the host).
  *   out:    receives the handle; free with cuboid_tables_free.

@@ -29,10 +29,10 @@ Readings where the paper is silent (each is also listed in the design notes):
   ``allow_diagonal`` adds the pairs p == q whatever their gcd.
 * Range bounds are inclusive; ``q_lt_p`` restricts a range to q < p (q <= p with
   ``allow_diagonal``).
-* The effective prime order is the caller's order, or with ``by_density`` the primes
-  sorted by decreasing fraction of unsolvable k in the reduced table v_r (ties: smaller
-  r first).  A pair's count goes to the first prime of the effective order that rejects
-  it.
+* The effective prime order is the caller's order, or the primes sorted by decreasing
+  fraction of unsolvable k in the reduced table v_r (count/r), or by the rejection rate
+  of a coprime pair (count/(r + 1)); ties: smaller r first.  A pair's count goes to the
+  first prime of the effective order that rejects it.
 * The reduced table v_r(k) = u_r(k, 1) is obtained by brute force over t~; the identity
   u_r(a, b) = v_r(a b^-1 mod r) for b != 0 and u_r(a, 0) = 0 (weighted homogeneity of
   Eq. 1.1: Q_{lp,lq}(l^2 t) = l^20 Q_pq(t)) is checked against brute-force full tables in
@@ -191,13 +191,23 @@ class Tables:
         return int(self.lookup(i, a, np.array([b], dtype=np.int64))[0])
 
 
-def effective_order(primes, unsolvable_counts, by_density: bool) -> list[int]:
-    """Caller order, or primes sorted by decreasing unsolvable fraction count/r
-    (exact rational comparison), ties by increasing r."""
+def effective_order(primes, unsolvable_counts, by_density) -> list[int]:
+    """The order in which the primes are tried.
+
+    * False / "given": the caller's order (the paper's ascending list, section 2);
+    * True / "density": decreasing unsolvable fraction count/r of the reduced table;
+    * "rate": decreasing rejection rate count/(r + 1) of a random coprime pair (given
+      gcd(p, q) = 1, r divides p with probability 1/(r + 1), likewise q, and otherwise
+      p/q mod r is uniform on the r - 1 nonzero residues, count of which are unsolvable).
+    Comparisons are exact (fractions); ties go to the smaller r."""
     idx = list(range(len(primes)))
-    if not by_density:
+    mode = {False: "given", True: "density"}.get(by_density, by_density)
+    if mode == "given":
         return idx
-    return sorted(idx, key=lambda i: (-Fraction(unsolvable_counts[i], primes[i]), primes[i]))
+    extra = 1 if mode == "rate" else 0
+    if mode not in ("density", "rate"):
+        raise ValueError(f"unknown order {by_density!r}")
+    return sorted(idx, key=lambda i: (-Fraction(unsolvable_counts[i], primes[i] + extra), primes[i]))
 
 
 # --------------------------------------------------------------------------------------

@@ -29,7 +29,7 @@ NOALLOC_MAX_RANGES = 4096
 STATUS_NAMES = {0: "OK", 1: "EBUSY", 2: "ERANGE", 6: "ENOTABLES", 7: "EINVAL", 8: "ENOMEM",
                 9: "ETIMEOUT", 10: "ECUDA", 11: "EOVERFLOW", 12: "EAGAIN", 13: "EVERIFY", 14: "ETOOLARGE"}
 
-ORDER_AS_GIVEN, ORDER_BY_DENSITY = 0x0, 0x1
+ORDER_AS_GIVEN, ORDER_BY_DENSITY, ORDER_BY_RATE = 0x0, 0x1, 0x4
 BUILD_REDUCED, BUILD_FULL = 0x0, 0x2
 Q_LT_P, ALLOW_DIAGONAL, ROWS_P, ROWS_Q = 0x1, 0x2, 0x4, 0x8
 MODE_PLAIN, MODE_BATCHED, MODE_COUNT_STEPS, MODE_TIME_SIEVE = 0x0, 0x1, 0x100, 0x200
@@ -58,7 +58,8 @@ class cuboid_root(C.Structure):
 
 class cuboid_tuning(C.Structure):
     _fields_ = [("block_threads", C.c_uint32), ("ctas_per_sm", C.c_uint32),
-                ("smem_primes", C.c_uint32), ("tiles_per_warp", C.c_uint32)]
+                ("smem_primes", C.c_uint32), ("tiles_per_warp", C.c_uint32),
+                ("hot_primes", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class cuboid_stats(C.Structure):
@@ -176,8 +177,8 @@ def cuboid_tables_copy_reduced(t, prime_idx: int, r: int) -> bytes:
     return bytes(buf)
 
 
-def cuboid_tables_set_tuning(t, block_threads=0, ctas_per_sm=0, smem_primes=0, tiles_per_warp=0):
-    tu = cuboid_tuning(block_threads, ctas_per_sm, smem_primes, tiles_per_warp)
+def cuboid_tables_set_tuning(t, block_threads=0, ctas_per_sm=0, smem_primes=0, tiles_per_warp=0, hot_primes=0):
+    tu = cuboid_tuning(block_threads, ctas_per_sm, smem_primes, tiles_per_warp, hot_primes, 0)
     _check(_lib.cuboid_tables_set_tuning(t, C.byref(tu)), "cuboid_tables_set_tuning")
 
 

@@ -106,7 +106,10 @@ struct SieveArgs {
   uint32_t n_trial;
   uint32_t range_first;
   uint32_t range_count;         // UINT32_MAX: read hdr->n_ranges
+  uint32_t n_hot;               // hot primes (0, 2, 4 or 6): the first n_hot of the effective order
+  uint32_t hot_r[6], hot_magic[6], hot_off[6], hot_W[6];
 };
+constexpr uint32_t kMaxHot = 6;
 
 struct VerifyArgs {
   const unsigned long long* surv;
@@ -133,9 +136,10 @@ cudaError_t verify_init_device();   // upload the 62-bit moduli (once per device
 
 // Sieve launch shape chosen from the tables' tuning (runtime.cu).
 struct LaunchShape {
-  uint32_t threads, blocks, n_smem, smem_words, target_tiles;
+  uint32_t threads, blocks, n_smem, smem_words, target_tiles, n_hot;
   size_t smem;
 };
+void fill_hot(SieveArgs& a, const cuboid_tables* t, const LaunchShape& L);
 LaunchShape launch_shape(const cuboid_tables* t);
 
 int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_t s,

@@ -105,6 +105,7 @@ extern "C" int cuboid_sieve_noalloc(const cuboid_tables* t, const cuboid_range* 
     a.n_trial = t->n_trial;
     a.range_first = 0;
     a.range_count = 0xFFFFFFFFu;
+    fill_hot(a, t, L);
     e = launch_sieve(a, false, L.blocks, L.threads, L.smem, s);
   }
   if (e == cudaSuccess) {

@@ -14,8 +14,9 @@ constexpr uint64_t kDefaultSurvCap = 1ull << 20;
 constexpr uint64_t kDefaultRootCap = 1ull << 16;
 constexpr uint32_t kDefaultThreads = 512;
 constexpr uint32_t kDefaultCtasPerSm = 2;
-constexpr uint32_t kDefaultTilesPerWarp = 8;
-constexpr size_t kDefaultTableSmem = 32 * 1024;
+constexpr uint32_t kDefaultTilesPerWarp = 3;
+constexpr uint32_t kDefaultHot = 4;
+constexpr size_t kDefaultTableSmem = 48 * 1024;
 
 }  // namespace cuboid
 
@@ -88,11 +89,27 @@ LaunchShape launch_shape(const cuboid_tables* t) {
   }
   L.n_smem = k;
   L.smem_words = (uint32_t)words;
+  // hot primes: an instantiated count (0, 2, 4, 6), all inside the shared-memory prefix
+  uint32_t hot = T.hot_primes ? T.hot_primes : kDefaultHot;
+  if (hot > k) hot = k;
+  if (hot > kMaxHot) hot = kMaxHot;
+  L.n_hot = hot & ~1u;
   L.smem = sieve_smem_bytes(L.smem_words, t->n, L.threads);
   L.blocks = (uint32_t)t->sms * ctas;
   const uint32_t tpw = T.tiles_per_warp ? T.tiles_per_warp : kDefaultTilesPerWarp;
   L.target_tiles = L.blocks * (L.threads / 32) * tpw;
   return L;
+}
+
+void fill_hot(SieveArgs& a, const cuboid_tables* t, const LaunchShape& L) {
+  a.n_hot = L.n_hot;
+  for (uint32_t h = 0; h < kMaxHot; ++h) {
+    const PrimeInfo pi = h < L.n_hot ? t->info[h] : PrimeInfo{1u, 0u, 0u, 0u};
+    a.hot_r[h] = pi.r;
+    a.hot_magic[h] = pi.magic;
+    a.hot_off[h] = pi.off;
+    a.hot_W[h] = pi.W;
+  }
 }
 
 static SieveArgs sieve_args(cuboid_result* r, const LaunchShape& L, uint32_t first, uint32_t count) {
@@ -114,6 +131,7 @@ static SieveArgs sieve_args(cuboid_result* r, const LaunchShape& L, uint32_t fir
   a.n_trial = t->n_trial;
   a.range_first = first;
   a.range_count = count;
+  fill_hot(a, t, L);
   return a;
 }
 

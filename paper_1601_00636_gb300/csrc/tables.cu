@@ -103,11 +103,13 @@ __global__ void k_full(const uint32_t* primes, const unsigned long long* foff, u
   }
 }
 
-// Effective order: order[rank] = caller index.
-__global__ void k_order(const uint32_t* primes, const uint32_t* unsolvable, uint32_t n, int by_density,
+// Effective order: order[rank] = caller index.  mode 0: caller order; 1: decreasing
+// count/r; 2: decreasing count/(r + 1), the rejection rate of a random coprime pair.
+__global__ void k_order(const uint32_t* primes, const uint32_t* unsolvable, uint32_t n, int mode,
                         uint32_t* order) {
+  const uint64_t d = mode == 2 ? 1 : 0;
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    if (!by_density) {
+    if (mode == 0) {
       order[i] = i;
       continue;
     }
@@ -115,7 +117,7 @@ __global__ void k_order(const uint32_t* primes, const uint32_t* unsolvable, uint
     uint32_t rank = 0;
     for (uint32_t j = 0; j < n; ++j) {
       const uint64_t cj = unsolvable[j], rj = primes[j];
-      const uint64_t lhs = cj * ri, rhs = ci * rj;  // fraction_j vs fraction_i
+      const uint64_t lhs = cj * (ri + d), rhs = ci * (rj + d);  // fraction_j vs fraction_i
       if (lhs > rhs || (lhs == rhs && rj < ri)) ++rank;
     }
     order[rank] = i;
@@ -206,7 +208,8 @@ int status_from_cuda(cudaError_t e) {
 int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_t s,
                  cuboid_tables** out) {
   if (!primes || !out || n == 0 || n > kMaxPrimes) return CUBOID_EINVAL;
-  if (flags & ~(CUBOID_ORDER_BY_DENSITY | CUBOID_BUILD_FULL)) return CUBOID_EINVAL;
+  if (flags & ~(CUBOID_ORDER_BY_DENSITY | CUBOID_ORDER_BY_RATE | CUBOID_BUILD_FULL)) return CUBOID_EINVAL;
+  if ((flags & CUBOID_ORDER_BY_DENSITY) && (flags & CUBOID_ORDER_BY_RATE)) return CUBOID_EINVAL;
   std::vector<uint32_t> pr(primes, primes + n);
   {
     std::vector<uint32_t> sorted = pr;
@@ -264,7 +267,8 @@ int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_
   CK(cudaMemsetAsync(d_cnt, 0, n * sizeof(uint32_t), s));
   k_reduced<<<n, 256, 0, s>>>(d_primes, d_voff, t->d_vbytes, d_cnt);
   CK(cudaGetLastError());
-  k_order<<<1, 1024, 0, s>>>(d_primes, d_cnt, n, (flags & CUBOID_ORDER_BY_DENSITY) ? 1 : 0, d_order);
+  k_order<<<1, 1024, 0, s>>>(d_primes, d_cnt, n,
+                             (flags & CUBOID_ORDER_BY_RATE) ? 2 : ((flags & CUBOID_ORDER_BY_DENSITY) ? 1 : 0), d_order);
   CK(cudaGetLastError());
   t->order.resize(n);
   t->unsolvable.resize(n);
@@ -422,7 +426,8 @@ extern "C" int cuboid_tables_copy_reduced(const cuboid_tables* t, uint32_t prime
 extern "C" int cuboid_tables_set_tuning(cuboid_tables* t, const cuboid_tuning* tune) {
   if (!t) return CUBOID_ENOTABLES;
   if (!tune) return CUBOID_EINVAL;
-  if (tune->block_threads % 32 || tune->block_threads > 1024 || tune->ctas_per_sm > 32)
+  if (tune->block_threads % 32 || tune->block_threads > 1024 || tune->ctas_per_sm > 32 || tune->reserved ||
+      tune->hot_primes > kMaxHot)
     return CUBOID_EINVAL;
   t->tuning = *tune;
   return CUBOID_OK;

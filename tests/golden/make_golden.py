@@ -33,6 +33,7 @@ def main():
     c2 = W.c2()
     dump("c2_as_given.json", c2["name"], c2["primes"], c2["ranges"])
     dump("c2_by_density.json", c2["name"], c2["primes"], c2["ranges"], by_density=True)
+    dump("c2_by_rate.json", c2["name"], c2["primes"], c2["ranges"], by_density="rate")
     dump("c4_rows.json", "c4 sampled rows", W.first_odd_primes(256), W.sampled_rows(1 << 20, 64))
     rects = [r for r in W.c3()["ranges"] if (r["p_hi"] - r["p_lo"] + 1) * (r["q_hi"] - r["q_lo"] + 1) <= 1 << 16][:64]
     dump("c3_small_rects.json", "c3 rectangles of area <= 2^16", W.first_odd_primes(128), rects)

@@ -36,6 +36,10 @@ def stream():
     return torch.cuda.current_stream()
 
 
+def _order_flag(cb, by_density):
+    return {False: cb.ORDER_AS_GIVEN, True: cb.ORDER_BY_DENSITY, "rate": cb.ORDER_BY_RATE}[by_density]
+
+
 def _golden(name):
     with open(os.path.join(GOLDEN, name)) as f:
         return json.load(f)
@@ -142,7 +146,7 @@ def test_c2_primes_full_tables_vs_oracle(cb, stream):
 @pytest.mark.parametrize("n", [24, 64, 128, 256])
 def test_effective_order(cb, stream, n):
     primes = W.first_odd_primes(n)
-    for flag, dens in ((cb.ORDER_AS_GIVEN, False), (cb.ORDER_BY_DENSITY, True)):
+    for flag, dens in ((cb.ORDER_AS_GIVEN, False), (cb.ORDER_BY_DENSITY, True), (cb.ORDER_BY_RATE, "rate")):
         t = cb.cuboid_tables_build(primes, flag, stream)
         try:
             got = cb.cuboid_tables_order(t)
@@ -155,11 +159,11 @@ def test_effective_order(cb, stream, n):
 # ---------------------------------------------------------------- K2-K4: sieve
 
 @pytest.mark.parametrize("mode", ["plain", "batched"])
-@pytest.mark.parametrize("dens", [False, True])
+@pytest.mark.parametrize("dens", [False, True, "rate"])
 def test_c1_parity(cb, stream, mode, dens):
     cfg = W.c1()
     primes = cfg["primes"]
-    t = cb.cuboid_tables_build(primes, cb.ORDER_BY_DENSITY if dens else 0, stream)
+    t = cb.cuboid_tables_build(primes, _order_flag(cb, dens), stream)
     try:
         st, got = _run(cb, t, len(primes), cfg["ranges"],
                        cb.MODE_BATCHED if mode == "batched" else cb.MODE_PLAIN, stream)
@@ -181,11 +185,11 @@ def test_c1_north_star_call(cb, stream, c1_tables):
     _check_against([got], [want])
 
 
-@pytest.mark.parametrize("name", ["c2_as_given.json", "c2_by_density.json"])
+@pytest.mark.parametrize("name", ["c2_as_given.json", "c2_by_density.json", "c2_by_rate.json"])
 @pytest.mark.parametrize("mode", ["plain", "batched"])
 def test_c2_parity(cb, stream, name, mode):
     g = _golden(name)
-    t = cb.cuboid_tables_build(g["primes"], cb.ORDER_BY_DENSITY if g["by_density"] else 0, stream)
+    t = cb.cuboid_tables_build(g["primes"], _order_flag(cb, g["by_density"]), stream)
     try:
         assert cb.cuboid_tables_order(t) == g["order"]
         st, got = _run(cb, t, len(g["primes"]), g["ranges"],
@@ -275,13 +279,16 @@ def test_transposed_rectangles(cb, stream, c1_tables):
 
 TUNINGS = [dict(), dict(block_threads=256, ctas_per_sm=1), dict(block_threads=1024, ctas_per_sm=1),
            dict(smem_primes=1), dict(smem_primes=64, ctas_per_sm=1, block_threads=512),
-           dict(tiles_per_warp=1), dict(tiles_per_warp=64, ctas_per_sm=4, block_threads=128)]
+           dict(tiles_per_warp=1), dict(tiles_per_warp=64, ctas_per_sm=4, block_threads=128),
+           dict(hot_primes=0), dict(hot_primes=2), dict(hot_primes=6, smem_primes=10),
+           dict(hot_primes=6, smem_primes=3)]
 
 
 @pytest.mark.parametrize("tune", TUNINGS)
-def test_tuning_invariance_c2(cb, stream, tune):
-    g = _golden("c2_as_given.json")
-    t = cb.cuboid_tables_build(g["primes"], 0, stream)
+@pytest.mark.parametrize("name", ["c2_as_given.json", "c2_by_rate.json"])
+def test_tuning_invariance_c2(cb, stream, tune, name):
+    g = _golden(name)
+    t = cb.cuboid_tables_build(g["primes"], _order_flag(cb, g["by_density"]), stream)
     try:
         cb.cuboid_tables_set_tuning(t, **tune)
         st, got = _run(cb, t, 64, g["ranges"], cb.MODE_BATCHED, stream)

@@ -202,6 +202,20 @@ def test_effective_order_by_density():
         fa, fb = cnt[a] / primes[a], cnt[b] / primes[b]
         assert fa > fb or (fa == fb and primes[a] < primes[b])
     assert O.effective_order(primes, cnt, False) == list(range(len(primes)))
+    rate = O.effective_order(primes, cnt, "rate")
+    for a, b in zip(rate, rate[1:]):
+        fa, fb = cnt[a] / (primes[a] + 1), cnt[b] / (primes[b] + 1)
+        assert fa > fb or (fa == fb and primes[a] < primes[b])
+
+
+def test_rejection_rate_matches_coprime_pairs():
+    """The rate count/(r + 1) is the fraction of coprime pairs a prime rejects: counted
+    by brute force over all coprime pairs of a large box, prime by prime."""
+    pairs = [(p, q) for p in range(1, 400) for q in range(1, 400) if p != q and math.gcd(p, q) == 1]
+    for r in (11, 13, 17, 19, 23):
+        T = O.Tables([r])
+        rej = sum(T.bit(0, p, q) for p, q in pairs)
+        assert abs(rej / len(pairs) - O.unsolvable_count(r) / (r + 1)) < 0.01
 
 
 # ---------------------------------------------------------------- sieve and totals
