@@ -324,7 +324,7 @@ def run_ours(args):
                        "form": "plain (one range per launch)", "l2": "flushed (256 MiB write) before each step",
                        "parallelism": f"replicas x{world}"},
             "bit_exact": bit_exact, "table_build_ms": table_ms,
-            "roofline": roofline, "clocks": clk, "gpu_launches": 4 * args.steps}
+            "roofline": roofline, "clocks": clk, "gpu_launches": 3 * args.steps}
 
     if not args.no_extras and rank == 0:
         line["e2e"] = e2e_leg(cb, torch, primes, rng, args)

@@ -94,7 +94,7 @@ typedef struct cuboid_tuning {
   uint32_t ctas_per_sm;     /* persistent CTAs per SM */
   uint32_t smem_primes;     /* how many leading primes (effective order) sit in shared memory */
   uint32_t tiles_per_warp;  /* target number of work tiles per warp (sets the tile size) */
-  uint32_t hot_primes;      /* leading primes tested without an early-exit check (0, 2, 4, 6) */
+  uint32_t hot_primes;      /* leading primes tested without an early-exit check (0..8) */
   uint32_t reserved;        /* must be 0 */
 } cuboid_tuning;
 

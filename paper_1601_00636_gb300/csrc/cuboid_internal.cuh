@@ -26,9 +26,9 @@ struct PrimeInfo {
 };
 
 // Window-row layout: row a of prime r holds W 32-bit words; bit j (0 <= j < 32 W) is
-// u_r(a, j mod r).  The 32 bits u_r(a, s), ..., u_r(a, s + 31 mod r) for any s < r are
-// a funnel shift of words s/32 and s/32 + 1.
-__host__ __device__ inline uint32_t row_words(uint32_t r) { return (r - 1) / 32 + 2; }
+// u_r(a, j mod r).  The 64 bits u_r(a, s), ..., u_r(a, s + 63 mod r) for any s < r are
+// two funnel shifts of words s/32, s/32 + 1 and s/32 + 2.
+__host__ __device__ inline uint32_t row_words(uint32_t r) { return (r - 1) / 32 + 3; }
 
 // One planned range.  32 bytes.
 struct TilePlan {
@@ -46,11 +46,8 @@ struct DevHeader {
   unsigned long long total_tiles;  // tiles of the running launch
   unsigned long long n_surv;       // survivors found (may exceed the capacity)
   unsigned long long n_roots;      // roots found (may exceed the capacity)
-  unsigned long long verified_lo;  // survivors [0, verified_lo) have been root-tested
   unsigned int status;             // kStatus* bits
-  unsigned int n_ranges;           // ranges of a batched launch (written with the ranges)
-  unsigned int verify_done;        // blocks of the running verify launch that finished
-  unsigned int pad;
+  unsigned int n_ranges;           // ranges of a batched launch
   unsigned long long stats[4];     // cuboid_stats fields
 };
 constexpr unsigned kStatusSurvOverflow = 1u;
@@ -106,10 +103,10 @@ struct SieveArgs {
   uint32_t n_trial;
   uint32_t range_first;
   uint32_t range_count;         // UINT32_MAX: read hdr->n_ranges
-  uint32_t n_hot;               // hot primes (0, 2, 4 or 6): the first n_hot of the effective order
-  uint32_t hot_r[6], hot_magic[6], hot_off[6], hot_W[6];
+  uint32_t n_hot;               // hot primes (0, 2, 4, 5, 6 or 8): the first n_hot of the effective order
+  uint32_t hot_r[8], hot_magic[8], hot_off[8], hot_W[8];
 };
-constexpr uint32_t kMaxHot = 6;
+constexpr uint32_t kMaxHot = 8;
 
 struct VerifyArgs {
   const unsigned long long* surv;
@@ -125,7 +122,7 @@ struct VerifyArgs {
 cudaError_t launch_plan(const cuboid_range* ranges, uint32_t first, uint32_t count,
                         DevHeader* hdr, TilePlan* plan, unsigned long long* counts,
                         unsigned long long* npairs, uint32_t n_primes, uint32_t target_tiles,
-                        cudaStream_t s);
+                        cudaStream_t s, bool reset);
 cudaError_t launch_reset(DevHeader* hdr, uint32_t n_ranges, cudaStream_t s);
 cudaError_t launch_sieve(const SieveArgs& a, bool count_steps, uint32_t blocks,
                          uint32_t threads, size_t smem, cudaStream_t s);

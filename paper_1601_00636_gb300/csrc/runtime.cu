@@ -15,7 +15,7 @@ constexpr uint64_t kDefaultRootCap = 1ull << 16;
 constexpr uint32_t kDefaultThreads = 512;
 constexpr uint32_t kDefaultCtasPerSm = 2;
 constexpr uint32_t kDefaultTilesPerWarp = 3;
-constexpr uint32_t kDefaultHot = 4;
+constexpr uint32_t kDefaultHot = 5;
 constexpr size_t kDefaultTableSmem = 48 * 1024;
 
 }  // namespace cuboid
@@ -89,11 +89,16 @@ LaunchShape launch_shape(const cuboid_tables* t) {
   }
   L.n_smem = k;
   L.smem_words = (uint32_t)words;
-  // hot primes: an instantiated count (0, 2, 4, 6), all inside the shared-memory prefix
+  // hot primes: an instantiated count (0, 2, 4, 5, 6, 8), all inside the shared-memory prefix
   uint32_t hot = T.hot_primes ? T.hot_primes : kDefaultHot;
   if (hot > k) hot = k;
   if (hot > kMaxHot) hot = kMaxHot;
-  L.n_hot = hot & ~1u;
+  static const uint32_t kInst[] = {8, 6, 5, 4, 2, 0};
+  for (uint32_t c : kInst)
+    if (c <= hot) {
+      L.n_hot = c;
+      break;
+    }
   L.smem = sieve_smem_bytes(L.smem_words, t->n, L.threads);
   L.blocks = (uint32_t)t->sms * ctas;
   const uint32_t tpw = T.tiles_per_warp ? T.tiles_per_warp : kDefaultTilesPerWarp;
@@ -163,7 +168,7 @@ static cudaError_t timing_events(cuboid_result* r, uint32_t launches) {
 static cudaError_t enqueue_batched(cuboid_result* r, const LaunchShape& L, bool steps, bool timed,
                                    cudaStream_t s) {
   cudaError_t e = launch_plan(r->d_ranges, 0, 0xFFFFFFFFu, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs,
-                              r->t->n, L.target_tiles, s);
+                              r->t->n, L.target_tiles, s, false);
   if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[0], s);
   if (e == cudaSuccess) e = launch_sieve(sieve_args(r, L, 0, 0xFFFFFFFFu), steps, L.blocks, L.threads, L.smem, s);
   if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[1], s);
@@ -171,6 +176,8 @@ static cudaError_t enqueue_batched(cuboid_result* r, const LaunchShape& L, bool 
   return e;
 }
 
+// Batched: reset + one graph (plan, persistent sieve, root test).  Plain: per range a
+// plan and a sieve launch (the first plan also clears the header), then one root test.
 static cudaError_t run_kernels(cuboid_result* r, uint32_t n, uint32_t mode, cudaStream_t s) {
   const bool steps = mode & CUBOID_MODE_COUNT_STEPS;
   const bool timed = mode & CUBOID_MODE_TIME_SIEVE;
@@ -183,9 +190,9 @@ static cudaError_t run_kernels(cuboid_result* r, uint32_t n, uint32_t mode, cuda
     e = timing_events(r, batched ? 1 : n);
     if (e != cudaSuccess) return e;
   }
-  e = launch_reset(r->d_hdr, n, s);  // zero the header, n_ranges = n
-  if (e != cudaSuccess) return e;
   if (batched) {
+    e = launch_reset(r->d_hdr, n, s);  // zero the header, n_ranges = n
+    if (e != cudaSuccess) return e;
     const int gi = (steps ? 1 : 0) + (timed ? 2 : 0);
     cudaGraphExec_t& g = r->graph[gi];
     if (g && std::memcmp(&r->graph_tuning[gi], &r->t->tuning, sizeof(cuboid_tuning)) != 0) {
@@ -211,13 +218,13 @@ static cudaError_t run_kernels(cuboid_result* r, uint32_t n, uint32_t mode, cuda
     return cudaGraphLaunch(g, s);
   }
   for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
-    e = launch_plan(r->d_ranges, i, 1, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs, r->t->n,
-                    L.target_tiles, s);
+    e = launch_plan(r->d_ranges, i, 1, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs, r->t->n, L.target_tiles,
+                    s, i == 0);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i], s);
     if (e == cudaSuccess) e = launch_sieve(sieve_args(r, L, i, 1), steps, L.blocks, L.threads, L.smem, s);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i + 1], s);
-    if (e == cudaSuccess) e = launch_verify(verify_args(r), verify_blocks(r->t), s);
   }
+  if (e == cudaSuccess) e = launch_verify(verify_args(r), verify_blocks(r->t), s);
   if (timed) r->timed_launches = n;
   return e;
 }

@@ -1,18 +1,21 @@
 // K2 + K3: the bit sieve of section 2 / the search loop of section 5, on the device.
 //
 // Work unit ("tile"): one row value x (p, or q when the rectangle is narrow in q) and a
-// chunk of consecutive 32-value words of the other coordinate y.  Each lane owns one
-// 32-bit word of y values (y0 = 32 w .. 32 w + 31) and carries an "alive" mask of the
+// chunk of consecutive 64-value words of the other coordinate y.  Each lane owns one
+// 64-bit word of y values (y0 = 64 w .. 64 w + 63) and carries an "alive" mask of the
 // pairs still in play:
 //   alive = in-range bits & ~(bits of y sharing a prime factor with x) & ~diagonal,
 // then for each prime of the effective order
 //   rej   = window(u_r row x mod r, starting at y0 mod r) & alive
 //   count[prime] += popc(rej);  alive &= ~rej
-// until every lane of the warp is empty (warp-uniform early exit).  The window is one
-// funnel shift of two 32-bit words of the window-row table (see cuboid_internal.cuh).
-// Survivors (alive bits after the last prime) are compacted with a warp prefix sum and
-// one atomic per warp.  Tiles come from a device queue (one atomic per tile), so the
-// same kernel serves one range per launch and thousands of ranges per launch.
+// The window is two funnel shifts of three 32-bit words of the window-row table (see
+// cuboid_internal.cuh).  The first K primes ("hot") are applied to every word without an
+// early-exit test, with their moduli in the constant bank and their counts in registers;
+// words still alive afterwards go to a per-warp queue and are finished 32 at a time
+// with a warp-uniform early exit.  Survivors (alive bits after the last prime) are
+// compacted with a warp prefix sum and one atomic per warp.  Tiles come from a device
+// queue (one atomic per tile), so one kernel serves one range per launch and thousands
+// of ranges per launch.
 #include "cuboid_internal.cuh"
 
 namespace cuboid {
@@ -20,23 +23,20 @@ namespace cuboid {
 namespace {
 
 constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr unsigned long long FULL64 = ~0ull;
 constexpr uint32_t kNoRange = 0xFFFFFFFFu;
-constexpr uint32_t kFlushTiles = 256;  // per-warp uint32 counters are flushed at least this often
-
-// n mod r for any 32-bit n, with magic = floor(2^32 / r): the estimate n*magic/2^32 is
-// floor(n/r) or one less, so one conditional subtraction finishes the residue.
-__device__ __forceinline__ uint32_t fast_mod(uint32_t n, uint32_t r, uint32_t magic) {
-  const uint32_t qt = __umulhi(n, magic);
-  const uint32_t rem = n - qt * r;
-  return rem >= r ? rem - r : rem;
-}
+constexpr uint32_t kFlushTiles = 256;       // per-warp uint32 counters are flushed at least this often
+constexpr uint32_t kMaxChunkWords = 32768;  // 64-value words per tile: at most 2^21 pairs
+constexpr uint32_t kQueue = 64;             // per-warp queue of words that outlive the hot primes
+constexpr int kFacRegs = 4;                 // odd factors whose per-lane offsets sit in registers
+constexpr uint32_t kLaneStride = 2048;      // a lane's next word starts 32 words x 64 values further on
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
   for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
   return v;
 }
 
-// ------------------------------------------------------------------ plan kernel
+// ------------------------------------------------------------------ reset and plan kernels
 
 __global__ void k_reset(DevHeader* hdr, uint32_t n_ranges) {
   DevHeader h = {};
@@ -44,18 +44,28 @@ __global__ void k_reset(DevHeader* hdr, uint32_t n_ranges) {
   *hdr = h;
 }
 
+// Plans ranges [first, first + count): row orientation, tile size and the inclusive
+// prefix sum of tiles; zeroes their counts and pair totals; resets the queue cursor.
+// count_arg == kNoRange: read the count from the header (batched launches).  reset:
+// also clear the header's counters (the first launch of a plain run).
 __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint32_t first,
                                                uint32_t count_arg, DevHeader* hdr, TilePlan* plan,
                                                unsigned long long* counts, unsigned long long* npairs,
-                                               uint32_t n_primes, uint32_t target_tiles) {
+                                               uint32_t n_primes, uint32_t target_tiles, uint32_t reset) {
   __shared__ unsigned long long s_words;
   __shared__ unsigned long long s_carry;
   __shared__ unsigned long long s_warp[32];
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t count = count_arg == kNoRange ? hdr->n_ranges : count_arg;
+  __syncthreads();
   if (tid == 0) {
     s_words = 0;
     s_carry = 0;
+    if (reset) {
+      DevHeader h = {};
+      h.n_ranges = count;
+      *hdr = h;
+    }
   }
   __syncthreads();
   unsigned long long my_words = 0;
@@ -81,19 +91,18 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
       P.y_lo = rows_q ? R.p_lo : R.q_lo;
       P.y_hi = rows_q ? R.p_hi : R.q_hi;
       P.flags = (fl & (CUBOID_Q_LT_P | CUBOID_ALLOW_DIAGONAL)) | (rows_q ? kRowsQ : 0u);
-      my_words += ((unsigned long long)(P.x_hi - P.x_lo) + 1) * ((P.y_hi >> 5) - (P.y_lo >> 5) + 1);
+      my_words += ((unsigned long long)(P.x_hi - P.x_lo) + 1) * ((P.y_hi >> 6) - (P.y_lo >> 6) + 1);
     }
-    P.chunk_words = 32;
+    P.chunk_words = 1;
     P.tile_end = 0;
     plan[first + k] = P;
   }
   my_words = warp_sum_u64(my_words);
-  if (lane == 0) atomicAdd(&s_words, my_words);
+  if (lane == 0 && my_words) atomicAdd(&s_words, my_words);
   __syncthreads();
   unsigned long long cw = (s_words + target_tiles - 1) / (target_tiles ? target_tiles : 1);
-  cw = (cw + 31) & ~31ull;
-  if (cw < 32) cw = 32;
-  if (cw > 65536) cw = 65536;  // keeps a warp's uint32 counters below 2^32 between flushes
+  if (cw < 1) cw = 1;
+  if (cw > kMaxChunkWords) cw = kMaxChunkWords;
 
   for (uint32_t base = 0; base < count; base += blockDim.x) {
     const uint32_t k = base + tid;
@@ -102,9 +111,8 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
     if (k < count) {
       P = plan[first + k];
       if (P.x_lo <= P.x_hi) {
-        const unsigned long long nw = (P.y_hi >> 5) - (P.y_lo >> 5) + 1;
-        unsigned long long chunk = (nw + 31) & ~31ull;
-        if (chunk > cw) chunk = cw;
+        const unsigned long long nw = (P.y_hi >> 6) - (P.y_lo >> 6) + 1;
+        const unsigned long long chunk = nw < cw ? nw : cw;
         P.chunk_words = (uint32_t)chunk;
         tiles = ((unsigned long long)(P.x_hi - P.x_lo) + 1) * ((nw + chunk - 1) / chunk);
       }
@@ -146,8 +154,23 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
 
 // ------------------------------------------------------------------ sieve kernel
 
-constexpr uint32_t kQueue = 64;    // per-warp queue of words that outlive the hot primes
-constexpr int kFacRegs = 4;        // odd factors of the row whose per-lane offsets sit in registers
+// Coprimality masks come from a small table in shared memory: for each odd prime f < 64
+// and offset t in [0, f) the 64-bit mask of bits t, t + f, t + 2f, ...; then the single
+// bits 1 << t for t in [0, 64) and an empty mask at index 64 (a factor f >= 64 hits a
+// 64-value word at most once).
+__constant__ uint32_t kSmallOddPrimes[17] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61};
+constexpr uint32_t odd_prime_sum_below(uint32_t lim) {
+  uint32_t s = 0;
+  for (uint32_t f = 3; f < lim; f += 2) {
+    bool prime = true;
+    for (uint32_t d = 3; d * d <= f; d += 2) prime = prime && (f % d != 0);
+    if (prime) s += f;
+  }
+  return s;
+}
+constexpr uint32_t kBitTab = odd_prime_sum_below(64);  // 499: masks of the odd primes below 64
+constexpr uint32_t kMaskTab = kBitTab + 65;            // entries of the mask table
+static_assert(kBitTab == 499, "mask table layout");
 
 struct WarpState {
   uint32_t cur_range;
@@ -176,56 +199,56 @@ __device__ __forceinline__ void flush_counts(WarpState& ws, uint32_t* wcnt, cons
   __syncwarp();
 }
 
-// Words that outlived the hot primes: up to 32 queued (y0, alive) entries, one per lane,
-// go through the remaining primes with a warp-uniform early exit; survivors are
-// compacted with a warp prefix sum and one atomic per warp.
+// n mod r for any 32-bit n, with magic = floor(2^32 / r): n - floor(n*magic/2^32) r is
+// n mod r or n mod r + r, and the unsigned minimum with itself minus r picks the residue.
+__device__ __forceinline__ uint32_t mod_min(uint32_t n, uint32_t r, uint32_t magic) {
+  const uint32_t e = n - __umulhi(n, magic) * r;
+  return min(e, e - r);
+}
+
+// Up to 32 queued words {x, y0, alive lo, alive hi} (one per lane) of range `range` go
+// through the primes [first, n) with a warp-uniform early exit; then the survivors are
+// compacted.
 template <bool kSteps>
 __device__ __forceinline__ void cold_batch(const SieveArgs& a, const PrimeInfo* s_info, const uint32_t* s_tab,
-                                           uint32_t* wcnt, const uint2* q, uint32_t cnt, uint32_t first,
-                                           uint32_t x, bool rows_q, uint32_t range, uint32_t rowoff_lane,
-                                           uint32_t lane, WarpState& ws, unsigned long long& st_wsteps,
-                                           unsigned long long& st_warpsteps) {
-  const uint2 e = lane < cnt ? q[lane] : make_uint2(0u, 0u);
-  const uint32_t y0 = e.x;
-  uint32_t alive = e.y;
+                                           uint32_t* wcnt, const uint4* q, uint32_t cnt, uint32_t first,
+                                           bool rows_q, uint32_t range, uint32_t lane, WarpState& ws,
+                                           unsigned long long& st_wsteps, unsigned long long& st_warpsteps) {
+  const uint4 e = lane < cnt ? q[lane] : make_uint4(0u, 0u, 0u, 0u);
+  const uint32_t x = e.x, y0 = e.y;
+  uint32_t al = e.z, ah = e.w;
   const uint32_t n = a.n_primes;
   uint32_t i = first;
-  for (; i < a.n_smem_primes; ++i) {
-    if (!__any_sync(FULL, alive)) break;
-    const PrimeInfo pi = s_info[i];
-    const uint32_t ro = (i < 32) ? __shfl_sync(FULL, rowoff_lane, i) : pi.off + fast_mod(x, pi.r, pi.magic) * pi.W;
-    const uint32_t s = fast_mod(y0, pi.r, pi.magic);
-    const uint32_t wi = ro + (s >> 5);
-    const uint32_t win = __funnelshift_r(s_tab[wi], s_tab[wi + 1], s);
-    const uint32_t rej = win & alive;
-    const uint32_t c = __reduce_add_sync(FULL, __popc(rej));
-    if (kSteps) {
-      st_wsteps += alive ? 1 : 0;
-      st_warpsteps++;
-    }
-    if (lane == 0 && c) wcnt[i] += c;
-    alive ^= rej;
-  }
   for (; i < n; ++i) {
-    if (!__any_sync(FULL, alive)) break;
+    if (!__any_sync(FULL, (al | ah) != 0u)) break;
     const PrimeInfo pi = s_info[i];
-    const uint32_t ro = (i < 32) ? __shfl_sync(FULL, rowoff_lane, i) : pi.off + fast_mod(x, pi.r, pi.magic) * pi.W;
-    const uint32_t s = fast_mod(y0, pi.r, pi.magic);
+    const uint32_t ro = pi.off + mod_min(x, pi.r, pi.magic) * pi.W;
+    const uint32_t s = mod_min(y0, pi.r, pi.magic);
     const uint32_t wi = ro + (s >> 5);
-    const uint32_t win = __funnelshift_r(__ldg(a.words + wi), __ldg(a.words + wi + 1), s);
-    const uint32_t rej = win & alive;
-    const uint32_t c = __reduce_add_sync(FULL, __popc(rej));
+    uint32_t w0, w1, w2;
+    if (i < a.n_smem_primes) {
+      w0 = s_tab[wi];
+      w1 = s_tab[wi + 1];
+      w2 = s_tab[wi + 2];
+    } else {
+      w0 = __ldg(a.words + wi);
+      w1 = __ldg(a.words + wi + 1);
+      w2 = __ldg(a.words + wi + 2);
+    }
+    const uint32_t rl = __funnelshift_r(w0, w1, s) & al, rh = __funnelshift_r(w1, w2, s) & ah;
+    const uint32_t c = __reduce_add_sync(FULL, __popc(rl) + __popc(rh));
     if (kSteps) {
-      st_wsteps += alive ? 1 : 0;
+      st_wsteps += (al | ah) ? 1 : 0;
       st_warpsteps++;
     }
     if (lane == 0 && c) wcnt[i] += c;
-    alive ^= rej;
+    al ^= rl;
+    ah ^= rh;
   }
   const uint32_t reached = i < n ? i : n - 1;
   if (reached > ws.imax) ws.imax = reached;
-  if (__any_sync(FULL, alive)) {
-    const uint32_t kk = __popc(alive);
+  if (__any_sync(FULL, (al | ah) != 0u)) {
+    const uint32_t kk = __popc(al) + __popc(ah);
     uint32_t incl = kk;
     for (int d = 1; d < 32; d <<= 1) {
       const uint32_t o = __shfl_up_sync(FULL, incl, d);
@@ -237,8 +260,9 @@ __device__ __forceinline__ void cold_batch(const SieveArgs& a, const PrimeInfo* 
     basepos = __shfl_sync(FULL, basepos, 31);
     unsigned long long pos = basepos + incl - kk;
     bool over = false;
+    unsigned long long alive = ((unsigned long long)ah << 32) | al;
     while (alive) {
-      const uint32_t b = __ffs(alive) - 1;
+      const uint32_t b = (uint32_t)__ffsll((long long)alive) - 1;
       alive &= alive - 1;
       const uint32_t y = y0 + b;
       const unsigned long long p = rows_q ? y : x, qq = rows_q ? x : y;
@@ -254,10 +278,27 @@ __device__ __forceinline__ void cold_batch(const SieveArgs& a, const PrimeInfo* 
   }
 }
 
+// Process full batches of 32 queued words (all of them when `all`).
+template <bool kSteps>
+__device__ __forceinline__ void drain(const SieveArgs& a, const PrimeInfo* s_info, const uint32_t* s_tab,
+                                      uint32_t* wcnt, uint4* q, uint32_t& qn, uint32_t first, bool rows_q,
+                                      uint32_t range, uint32_t lane, WarpState& ws, unsigned long long& st_wsteps,
+                                      unsigned long long& st_warpsteps, bool all) {
+  while (qn >= 32 || (all && qn > 0)) {
+    const uint32_t cnt = qn < 32 ? qn : 32;
+    cold_batch<kSteps>(a, s_info, s_tab, wcnt, q, cnt, first, rows_q, range, lane, ws, st_wsteps, st_warpsteps);
+    const uint32_t rest = qn - cnt;
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < rest) e = q[32 + lane];
+    __syncwarp();
+    if (lane < rest) q[lane] = e;
+    __syncwarp();
+    qn = rest;
+  }
+}
+
 // K: number of "hot" primes (the first K of the effective order, all resident in shared
-// memory).  Every word goes through them without an early-exit test, their moduli are
-// kernel parameters (constant bank) and their counts accumulate in registers; words
-// still alive afterwards are queued and finished by cold_batch.
+// memory).
 template <bool kSteps, int K>
 __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
   extern __shared__ uint4 smem_raw[];
@@ -265,39 +306,58 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
   const uint32_t warps = blockDim.x >> 5;
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t lanemask_lt = (1u << lane) - 1u;
-  PrimeInfo* s_info = reinterpret_cast<PrimeInfo*>(smem_raw);
-  uint4* s_fac_all = smem_raw + n;                                                   // [warps][kMaxFactors]
-  uint2* s_queue_all = reinterpret_cast<uint2*>(s_fac_all + warps * kMaxFactors);    // [warps][kQueue]
-  uint32_t* s_pat = reinterpret_cast<uint32_t*>(s_queue_all + warps * kQueue);       // [32]
-  uint32_t* s_cnt_all = s_pat + 32;                                                  // [warps][n]
-  uint32_t* s_tab = s_cnt_all + warps * n;                                           // [smem_words]
+  PrimeInfo* s_info = reinterpret_cast<PrimeInfo*>(smem_raw);                       // [n]
+  uint4* s_fac_all = smem_raw + n;                                                    // [warps][kMaxFactors]
+  uint4* s_queue_all = s_fac_all + warps * kMaxFactors;                              // [warps][kQueue]
+  uint2* s_mtab = reinterpret_cast<uint2*>(s_queue_all + warps * kQueue);            // [kMaskTab]
+  uint32_t* s_foff = reinterpret_cast<uint32_t*>(s_mtab + kMaskTab);                 // [64]
+  uint32_t* s_cnt_all = s_foff + 64;                                                  // [warps][n]
+  uint32_t* s_tab = s_cnt_all + warps * n;                                            // [smem_words]
 
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) s_info[i] = a.info[i];
   for (uint32_t i = threadIdx.x; i < warps * n; i += blockDim.x) s_cnt_all[i] = 0;
-  if (threadIdx.x < 32) {  // bits 0, f, 2f, ... of a 32-bit word, for odd f < 32
-    uint32_t pat = 0;
-    const uint32_t f = threadIdx.x;
-    if (f >= 3 && (f & 1))
-      for (uint32_t j = 0; j < 32; j += f) pat |= 1u << j;
-    s_pat[f] = pat;
+  for (uint32_t i = threadIdx.x; i < kMaskTab; i += blockDim.x) {
+    unsigned long long m = 0;
+    if (i >= kBitTab) {
+      if (i - kBitTab < 64) m = 1ull << (i - kBitTab);
+    } else {
+      uint32_t base = 0, j = 0;
+      while (base + kSmallOddPrimes[j] <= i) base += kSmallOddPrimes[j++];
+      const uint32_t f = kSmallOddPrimes[j], t = i - base;
+      for (uint32_t b = t; b < 64; b += f) m |= 1ull << b;
+    }
+    s_mtab[i] = make_uint2((uint32_t)m, (uint32_t)(m >> 32));
+  }
+  if (threadIdx.x < 64) {
+    uint32_t base = 0, off = kBitTab;
+    for (uint32_t j = 0; j < 17; ++j) {
+      if (kSmallOddPrimes[j] == threadIdx.x) off = base;
+      base += kSmallOddPrimes[j];
+    }
+    s_foff[threadIdx.x] = off;
   }
   for (uint32_t i = threadIdx.x; i < a.smem_words; i += blockDim.x) s_tab[i] = __ldg(a.words + i);
   __syncthreads();
 
   uint4* s_fac = s_fac_all + wid * kMaxFactors;
-  uint2* s_queue = s_queue_all + wid * kQueue;
+  uint4* s_queue = s_queue_all + wid * kQueue;
   uint32_t* wcnt = s_cnt_all + wid * n;
   const uint32_t count = a.range_count == kNoRange ? a.hdr->n_ranges : a.range_count;
   const unsigned long long total = a.hdr->total_tiles;
 
   WarpState ws{kNoRange, 0, 0, 0};
   unsigned long long st_words = 0, st_wsteps = 0, st_warpsteps = 0, st_tiles = 0;
+  uint32_t qn = 0;       // queued words (warp-uniform), all of range ws.cur_range
+  bool q_rows = false;   // orientation of the queued words
+
+  unsigned long long next = 0;
+  if (lane == 0) next = atomicAdd(&a.hdr->cursor, 1ull);
+  next = __shfl_sync(FULL, next, 0);
 
   for (;;) {
-    unsigned long long tile = 0;
-    if (lane == 0) tile = atomicAdd(&a.hdr->cursor, 1ull);
-    tile = __shfl_sync(FULL, tile, 0);
+    const unsigned long long tile = next;
     if (tile >= total) break;
+    if (lane == 0) next = atomicAdd(&a.hdr->cursor, 1ull);  // prefetch the next tile
 
     uint32_t k = a.range_first;
     if (count > 1) {  // first range with tile_end > tile
@@ -311,16 +371,19 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
     const TilePlan P = a.plan[k];
     const unsigned long long tbeg = (k == a.range_first) ? 0ull : a.plan[k - 1].tile_end;
     if (k != ws.cur_range || ws.tiles_since_flush >= kFlushTiles) {
+      drain<kSteps>(a, s_info, s_tab, wcnt, s_queue, qn, K, q_rows, ws.cur_range, lane, ws, st_wsteps,
+                    st_warpsteps, true);
       flush_counts(ws, wcnt, a, lane);
       ws.cur_range = k;
     }
     ws.tiles_since_flush++;
 
     const bool rows_q = P.flags & kRowsQ;
+    q_rows = rows_q;
     const bool tri = P.flags & CUBOID_Q_LT_P;
     const uint32_t diag = (P.flags & CUBOID_ALLOW_DIAGONAL) ? 1u : 0u;
-    const uint32_t wbox_lo = P.y_lo >> 5;
-    const uint32_t nw = (P.y_hi >> 5) - wbox_lo + 1;
+    const uint32_t wbox_lo = P.y_lo >> 6;
+    const uint32_t nw = (P.y_hi >> 6) - wbox_lo + 1;
     const uint32_t chunks = (nw + P.chunk_words - 1) / P.chunk_words;
     const unsigned long long local = tile - tbeg;
     unsigned long long row_idx;
@@ -346,17 +409,20 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
         if (lim > ylo) ylo = lim;
       }
     }
-    if (ylo > yhi) continue;
-    const uint32_t wlo = (uint32_t)(ylo >> 5), whi = (uint32_t)(yhi >> 5);
+    const uint32_t wlo = (uint32_t)(ylo >> 6), whi = (uint32_t)(yhi >> 6);
     const uint32_t c0 = wbox_lo + chunk * P.chunk_words;
     const uint32_t c1 = c0 + P.chunk_words - 1;
     const uint32_t wbeg = c0 > wlo ? c0 : wlo;
     const uint32_t wend = c1 < whi ? c1 : whi;
-    if (wbeg > wend) continue;
+    if (ylo > yhi || wbeg > wend) {
+      next = __shfl_sync(FULL, next, 0);
+      continue;
+    }
     if (kSteps) st_tiles++;
-    const uint32_t lo_mask = FULL << (uint32_t)(ylo & 31);
-    const uint32_t hi_mask = FULL >> (31 - (uint32_t)(yhi & 31));
-    const uint32_t dword = x >> 5, dbit = 1u << (x & 31);
+    const unsigned long long lo_mask = FULL64 << (uint32_t)(ylo & 63);
+    const unsigned long long hi_mask = FULL64 >> (63 - (uint32_t)(yhi & 63));
+    const uint32_t dword = x >> 6;
+    const uint32_t dbit_lo = (x & 32) ? 0u : 1u << (x & 31), dbit_hi = (x & 32) ? 1u << (x & 31) : 0u;
 
     // ---- distinct odd prime factors of x (warp-cooperative trial division)
     uint32_t nfo = 0;
@@ -380,13 +446,15 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
           const uint32_t f = __shfl_sync(FULL, tp.f, b);
           const uint32_t inv = __shfl_sync(FULL, tp.inv, b);
           const uint32_t lim = __shfl_sync(FULL, tp.lim, b);
-          while (m * inv <= lim) m *= inv;   // exact division by f
-          if (lane == 0) s_fac[nfo] = make_uint4(f, 0xFFFFFFFFu / f, f < 32 ? s_pat[f] : 1u, 1024u % f);
+          while (m * inv <= lim) m *= inv;  // exact division by f
+          if (lane == 0)
+            s_fac[nfo] = make_uint4(f, kLaneStride % f, f < 64 ? s_foff[f] : kBitTab, f < 64 ? f - 1 : 64u);
           ++nfo;
         }
       }
       if (m > 1) {
-        if (lane == 0) s_fac[nfo] = make_uint4(m, 0xFFFFFFFFu / m, m < 32 ? s_pat[m] : 1u, 1024u % m);
+        if (lane == 0)
+          s_fac[nfo] = make_uint4(m, kLaneStride % m, m < 64 ? s_foff[m] : kBitTab, m < 64 ? m - 1 : 64u);
         ++nfo;
       }
       __syncwarp();
@@ -394,99 +462,92 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
     // per-lane offset of the first multiple of each odd factor in the lane's first word
     uint32_t tf[kFacRegs];
     {
-      const uint32_t y0f = (wbeg + lane) << 5;
+      const uint32_t y0f = (wbeg + lane) << 6;
 #pragma unroll
       for (int i = 0; i < kFacRegs; ++i) {
         tf[i] = 0;
         if ((uint32_t)i < nfo) {
-          const uint4 fc = s_fac[i];
-          const uint32_t s = fast_mod(y0f, fc.x, fc.y);
-          tf[i] = s ? fc.x - s : 0u;
+          const uint32_t f = s_fac[i].x;
+          const uint32_t s = y0f % f;
+          tf[i] = s ? f - s : 0u;
         }
       }
     }
 
-    // ---- row offsets: hot primes in registers, the first 32 primes one per lane
+    // ---- row offsets of the hot primes
     uint32_t rb[K > 0 ? K : 1];
 #pragma unroll
-    for (int h = 0; h < K; ++h) rb[h] = a.hot_off[h] + fast_mod(x, a.hot_r[h], a.hot_magic[h]) * a.hot_W[h];
-    uint32_t rowoff_lane = 0;
-    if (lane < n) {
-      const PrimeInfo pi = s_info[lane];
-      rowoff_lane = pi.off + fast_mod(x, pi.r, pi.magic) * pi.W;
-    }
+    for (int h = 0; h < K; ++h) rb[h] = a.hot_off[h] + mod_min(x, a.hot_r[h], a.hot_magic[h]) * a.hot_W[h];
 
     uint32_t hcnt[K > 0 ? K : 1];
 #pragma unroll
     for (int h = 0; h < (K > 0 ? K : 1); ++h) hcnt[h] = 0;
     uint32_t tile_pairs = 0;
-    uint32_t qn = 0;
 
     for (uint32_t wb = wbeg; wb <= wend; wb += 32) {
       const uint32_t w = wb + lane;
-      const uint32_t y0 = w << 5;
-      uint32_t alive = 0;
+      const uint32_t y0 = w << 6;
+      uint32_t al = 0, ah = 0;
       if (w <= wend) {
-        uint32_t rm = FULL;
+        unsigned long long rm = FULL64;
         if (w == wlo) rm &= lo_mask;
         if (w == whi) rm &= hi_mask;
-        alive = has2 ? (rm & 0xAAAAAAAAu) : rm;  // y0 is even: even y at even bit positions
+        const uint32_t rml = (uint32_t)rm, rmh = (uint32_t)(rm >> 32);
+        al = has2 ? (rml & 0xAAAAAAAAu) : rml;  // y0 is even: even y at even bits
+        ah = has2 ? (rmh & 0xAAAAAAAAu) : rmh;
 #pragma unroll
         for (int i = 0; i < kFacRegs; ++i) {
           if ((uint32_t)i < nfo) {
-            const uint4 fc = s_fac[i];
-            if (tf[i] < 32) alive &= ~(fc.z << tf[i]);
-            const uint32_t tn = tf[i] - fc.w;  // the lane's next word starts 1024 further on
-            tf[i] = (int)tn < 0 ? tn + fc.x : tn;
+            const uint4 fc = s_fac[i];  // {f, 2048 mod f, table base, cap}
+            const uint2 mk = s_mtab[fc.z + min(tf[i], fc.w)];
+            al &= ~mk.x;
+            ah &= ~mk.y;
+            // the lane's next word starts 2048 further on: t <- (t - 2048) mod f
+            tf[i] = tf[i] >= fc.y ? tf[i] - fc.y : tf[i] - fc.y + fc.x;
           }
         }
         for (uint32_t i = kFacRegs; i < nfo; ++i) {
           const uint4 fc = s_fac[i];
-          const uint32_t s = fast_mod(y0, fc.x, fc.y);
-          const uint32_t j0 = s ? fc.x - s : 0u;
-          if (j0 < 32) alive &= ~(fc.z << j0);
+          const uint32_t s = y0 % fc.x;
+          const uint32_t t = s ? fc.x - s : 0u;
+          const uint2 mk = s_mtab[fc.z + min(t, fc.w)];
+          al &= ~mk.x;
+          ah &= ~mk.y;
         }
         if (w == dword) {
-          alive &= ~dbit;
-          if (diag) alive |= dbit & rm;
+          al &= ~dbit_lo;
+          ah &= ~dbit_hi;
+          if (diag) {
+            al |= dbit_lo & rml;
+            ah |= dbit_hi & rmh;
+          }
         }
-        tile_pairs += __popc(alive);
-        if (kSteps) st_words += alive ? 1 : 0;
+        tile_pairs += __popc(al) + __popc(ah);
+        if (kSteps) st_words += (al | ah) ? 1 : 0;
       }
       // hot primes: no early-exit test
 #pragma unroll
       for (int h = 0; h < K; ++h) {
-        if (kSteps) st_wsteps += alive ? 1 : 0;
-        const uint32_t s = fast_mod(y0, a.hot_r[h], a.hot_magic[h]);
-        const uint32_t wi = rb[h] + (s >> 5);
-        const uint32_t win = __funnelshift_r(s_tab[wi], s_tab[wi + 1], s);
-        const uint32_t rej = win & alive;
-        hcnt[h] += __popc(rej);
-        alive ^= rej;
+        if (kSteps) st_wsteps += (al | ah) ? 1 : 0;
+        const uint32_t s = mod_min(y0, a.hot_r[h], a.hot_magic[h]);
+        const uint32_t* tp = s_tab + rb[h] + (s >> 5);
+        const uint32_t w0 = tp[0], w1 = tp[1], w2 = tp[2];
+        const uint32_t rl = __funnelshift_r(w0, w1, s) & al, rh = __funnelshift_r(w1, w2, s) & ah;
+        hcnt[h] += __popc(rl) + __popc(rh);
+        al ^= rl;
+        ah ^= rh;
       }
       if (kSteps) st_warpsteps += K;
       // queue the words still alive
-      const uint32_t bal = __ballot_sync(FULL, alive != 0u);
+      const uint32_t bal = __ballot_sync(FULL, (al | ah) != 0u);
       if (bal) {
-        if (alive) s_queue[qn + __popc(bal & lanemask_lt)] = make_uint2(y0, alive);
+        if (al | ah) s_queue[qn + __popc(bal & lanemask_lt)] = make_uint4(x, y0, al, ah);
         qn += __popc(bal);
         __syncwarp();
-        if (qn >= 32) {
-          cold_batch<kSteps>(a, s_info, s_tab, wcnt, s_queue, 32, K, x, rows_q, k, rowoff_lane, lane, ws,
-                             st_wsteps, st_warpsteps);
-          const uint32_t rest = qn - 32;
-          uint2 e = make_uint2(0u, 0u);
-          if (lane < rest) e = s_queue[32 + lane];
-          __syncwarp();
-          if (lane < rest) s_queue[lane] = e;
-          __syncwarp();
-          qn = rest;
-        }
+        drain<kSteps>(a, s_info, s_tab, wcnt, s_queue, qn, K, rows_q, k, lane, ws, st_wsteps, st_warpsteps,
+                      false);
       }
     }
-    if (qn)
-      cold_batch<kSteps>(a, s_info, s_tab, wcnt, s_queue, qn, K, x, rows_q, k, rowoff_lane, lane, ws, st_wsteps,
-                         st_warpsteps);
     // tile totals
 #pragma unroll
     for (int h = 0; h < K; ++h) {
@@ -498,7 +559,10 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
     }
     ws.npairs += __reduce_add_sync(FULL, tile_pairs);
     __syncwarp();
+    next = __shfl_sync(FULL, next, 0);
   }
+  drain<kSteps>(a, s_info, s_tab, wcnt, s_queue, qn, K, q_rows, ws.cur_range, lane, ws, st_wsteps, st_warpsteps,
+                true);
   flush_counts(ws, wcnt, a, lane);
   if (kSteps) {
     const unsigned long long w = warp_sum_u64(st_words), s = warp_sum_u64(st_wsteps);
@@ -511,34 +575,38 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
   }
 }
 
-}  // namespace
-
-size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads) {
-  const uint32_t warps = threads / 32;
-  return (size_t)n_primes * sizeof(PrimeInfo) + (size_t)warps * kMaxFactors * sizeof(uint4) +
-         (size_t)warps * kQueue * sizeof(uint2) + 32 * sizeof(uint32_t) +
-         (size_t)warps * n_primes * sizeof(uint32_t) + (size_t)smem_words * sizeof(uint32_t);
-}
-
-namespace {
 template <bool S>
 cudaError_t set_attr_all(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(k_sieve<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  const int b = (int)bytes;
+  cudaError_t e = cudaFuncSetAttribute(k_sieve<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   return e;
 }
+
 template <bool S>
 void launch_k(const SieveArgs& a, uint32_t blocks, uint32_t threads, size_t smem, cudaStream_t s) {
   switch (a.n_hot) {
+    case 8: k_sieve<S, 8><<<blocks, threads, smem, s>>>(a); break;
     case 6: k_sieve<S, 6><<<blocks, threads, smem, s>>>(a); break;
+    case 5: k_sieve<S, 5><<<blocks, threads, smem, s>>>(a); break;
     case 4: k_sieve<S, 4><<<blocks, threads, smem, s>>>(a); break;
     case 2: k_sieve<S, 2><<<blocks, threads, smem, s>>>(a); break;
     default: k_sieve<S, 0><<<blocks, threads, smem, s>>>(a); break;
   }
 }
+
 }  // namespace
+
+size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads) {
+  const uint32_t warps = threads / 32;
+  return (size_t)n_primes * sizeof(PrimeInfo) + (size_t)warps * kMaxFactors * sizeof(uint4) +
+         (size_t)warps * kQueue * sizeof(uint4) + kMaskTab * sizeof(uint2) + 64 * sizeof(uint32_t) +
+         (size_t)warps * n_primes * sizeof(uint32_t) + (size_t)smem_words * sizeof(uint32_t);
+}
 
 cudaError_t sieve_set_smem_limit(bool count_steps, size_t bytes) {
   return count_steps ? set_attr_all<true>(bytes) : set_attr_all<false>(bytes);
@@ -551,8 +619,9 @@ cudaError_t launch_reset(DevHeader* hdr, uint32_t n_ranges, cudaStream_t s) {
 
 cudaError_t launch_plan(const cuboid_range* ranges, uint32_t first, uint32_t count, DevHeader* hdr,
                         TilePlan* plan, unsigned long long* counts, unsigned long long* npairs,
-                        uint32_t n_primes, uint32_t target_tiles, cudaStream_t s) {
-  k_plan<<<1, 1024, 0, s>>>(ranges, first, count, hdr, plan, counts, npairs, n_primes, target_tiles);
+                        uint32_t n_primes, uint32_t target_tiles, cudaStream_t s, bool reset) {
+  k_plan<<<1, 1024, 0, s>>>(ranges, first, count, hdr, plan, counts, npairs, n_primes, target_tiles,
+                            reset ? 1u : 0u);
   return cudaGetLastError();
 }
 

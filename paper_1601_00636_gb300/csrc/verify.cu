@@ -376,13 +376,12 @@ __device__ unsigned __int128 isqrt192(const U192& u) {
 }
 
 __global__ void __launch_bounds__(64) k_verify(VerifyArgs a) {
-  const ull lo = a.hdr->verified_lo;
   ull n = a.hdr->n_surv;
   if (n > a.surv_cap) n = a.surv_cap;
   Ctx C;
   Isolator iso;
   iso.C = &C;
-  for (ull idx = lo + blockIdx.x * (ull)blockDim.x + threadIdx.x; idx < n;
+  for (ull idx = blockIdx.x * (ull)blockDim.x + threadIdx.x; idx < n;
        idx += (ull)gridDim.x * blockDim.x) {
     const ull rec = a.surv[idx];
     const uint32_t p = (uint32_t)(rec >> 32), q = (uint32_t)rec;
@@ -412,14 +411,6 @@ __global__ void __launch_bounds__(64) k_verify(VerifyArgs a) {
       } else {
         atomicOr(&a.hdr->status, kStatusRootOverflow);
       }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&a.hdr->verify_done, 1u) == gridDim.x - 1) {
-      a.hdr->verified_lo = n;
-      a.hdr->verify_done = 0;
     }
   }
 }

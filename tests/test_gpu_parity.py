@@ -240,7 +240,9 @@ def _edge_ranges():
         R(999983, 999983, 999000, 1000100, allow_diagonal=True),
         R(2 * 3 * 5 * 7 * 11 * 13 * 17 * 19 * 23, 2 * 3 * 5 * 7 * 11 * 13 * 17 * 19 * 23, 1, 5000),
         R(65521 * 65519, 65521 * 65519, 65000, 66000),
-        R(4294967294, 4294967294, 1, 3000), R(200, 260, 1, 5000, q_lt_p=True), R(1, 5000, 200, 210), R(3, 3000, 2, 3001, q_lt_p=True, allow_diagonal=True),
+        R(4294967294, 4294967294, 1, 3000), R(200, 260, 1, 5000, q_lt_p=True),
+        R(61, 61, 1, 20000), R(122, 122, 1, 20000), R(61 * 67, 61 * 67, 1, 20000), R(183, 183, 1, 9000),
+        R(4294967291, 4294967291, 1, 70000), R(2 * 2147483647, 2 * 2147483647, 65536, 140000), R(1, 5000, 200, 210), R(3, 3000, 2, 3001, q_lt_p=True, allow_diagonal=True),
     ]
 
 
