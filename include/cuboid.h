@@ -145,6 +145,17 @@ int cuboid_tables_copy_reduced(const cuboid_tables* t, uint32_t prime_idx, uint8
 int cuboid_tables_set_tuning(cuboid_tables* t, const cuboid_tuning* tune);
 int cuboid_tables_get_tuning(const cuboid_tables* t, cuboid_tuning* tune);
 
+/* Autotuner: time kernel shapes (hot primes, tiles per warp, threads per CTA, CTAs per
+ * SM, primes in shared memory) by coordinate descent on these very ranges (host array,
+ * n >= 1, mode CUBOID_MODE_PLAIN or CUBOID_MODE_BATCHED), set the fastest on the tables
+ * and return it with its time in milliseconds (either pointer may be NULL).  Every
+ * candidate must give the same counts, pair totals and survivor/root totals; otherwise
+ * the tables keep their previous shape and EVERIFY is returned.  cache_path (may be
+ * NULL): a text file of earlier results keyed by device name, prime list, ranges and
+ * mode; a hit skips the search, a new result is appended.  Synchronous on stream. */
+int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uint32_t n, uint32_t mode, void* stream,
+                    const char* cache_path, cuboid_tuning* best, float* best_ms);
+
 /* Free the tables.  Returns EBUSY (and frees nothing) while a server uses them, like
  * the paper's Release call that refuses while a search runs (section 5). */
 int cuboid_tables_free(cuboid_tables* t);

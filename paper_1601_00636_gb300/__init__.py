@@ -78,6 +78,8 @@ _SIGS = {
     "cuboid_tables_set_tuning": (C.c_int, [_P, C.POINTER(cuboid_tuning)]),
     "cuboid_tables_get_tuning": (C.c_int, [_P, C.POINTER(cuboid_tuning)]),
     "cuboid_tables_free": (C.c_int, [_P]),
+    "cuboid_autotune": (C.c_int, [_P, C.POINTER(cuboid_range), _u32, _u32, _P, C.c_char_p,
+                                  C.POINTER(cuboid_tuning), C.POINTER(C.c_float)]),
     "cuboid_result_create": (C.c_int, [_P, _u32, _u64, _u64, C.POINTER(_P)]),
     "cuboid_sieve": (C.c_int, [_P, _u32, _u32, _u32, _u32, _u32, _P, C.POINTER(_P)]),
     "cuboid_sieve_batch": (C.c_int, [_P, C.POINTER(cuboid_range), _u32, _P, C.POINTER(_P)]),
@@ -186,6 +188,17 @@ def cuboid_tables_get_tuning(t) -> dict:
     tu = cuboid_tuning()
     _check(_lib.cuboid_tables_get_tuning(t, C.byref(tu)), "cuboid_tables_get_tuning")
     return {k: getattr(tu, k) for k, _ in cuboid_tuning._fields_}
+
+
+def cuboid_autotune(t, ranges, mode=MODE_BATCHED, stream=None, cache_path=None):
+    """Pick the fastest kernel shape for these ranges; returns (tuning dict, ms)."""
+    arr = _ranges_array(ranges)
+    tu = cuboid_tuning()
+    ms = C.c_float()
+    cp = cache_path.encode() if cache_path else None
+    _check(_lib.cuboid_autotune(t, arr, len(arr), mode, _stream(stream), cp, C.byref(tu), C.byref(ms)),
+           "cuboid_autotune")
+    return {k: getattr(tu, k) for k, _ in cuboid_tuning._fields_}, ms.value
 
 
 def cuboid_tables_free(t) -> int:

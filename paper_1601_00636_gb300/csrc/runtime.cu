@@ -426,6 +426,17 @@ int result_wait(cuboid_result* r) {
   return st;
 }
 
+int result_snapshot(cuboid_result* r, std::vector<unsigned long long>& counts,
+                    std::vector<unsigned long long>& npairs, unsigned long long& n_surv,
+                    unsigned long long& n_roots) {
+  if (!r || !r->fetched) return CUBOID_EINVAL;
+  counts.assign(r->counts.begin(), r->counts.end());
+  npairs.assign(r->npairs.begin(), r->npairs.end());
+  n_surv = r->h_hdr ? r->h_hdr->n_surv : 0;
+  n_roots = r->h_hdr ? r->h_hdr->n_roots : 0;
+  return CUBOID_OK;
+}
+
 bool result_event_done(cuboid_result* r) { return cudaEventQuery(r->done) != cudaErrorNotReady; }
 
 cuboid_result* result_host_only(const cuboid_tables* t, uint64_t npairs, const uint64_t* counts,

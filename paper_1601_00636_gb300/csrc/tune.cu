@@ -1,0 +1,202 @@
+// K6: autotuner of the sieve kernel shape.
+//
+// Coordinate descent over the kernel-shape knobs (hot primes, tiles per warp, threads per
+// CTA, CTAs per SM, primes staged in shared memory), timing each candidate on the
+// caller's own ranges with CUDA events.  Every candidate's counts, pair totals and
+// survivor/root totals must equal the first candidate's (the arithmetic never depends
+// on the shape); a mismatch is reported as CUBOID_EVERIFY.  The winner is set on the
+// tables and, with a cache path, remembered in a text file keyed by the device name,
+// the prime list (in its effective order), the ranges and the mode.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cuboid_internal.cuh"
+
+struct cuboid_result;
+namespace cuboid {
+int result_create(const cuboid_tables* t, uint32_t max_ranges, uint64_t surv_cap, uint64_t root_cap,
+                  cuboid_result** out);
+int sieve_into(cuboid_result* r, const cuboid_range* ranges, uint32_t n, uint32_t mode, cudaStream_t s,
+               bool device_ranges, bool download);
+int result_wait(cuboid_result* r);
+}  // namespace cuboid
+
+using namespace cuboid;
+
+namespace {
+
+uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+std::string cache_key(const cuboid_tables* t, const cuboid_range* ranges, uint32_t n, uint32_t mode) {
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, t->device);
+  std::vector<uint32_t> eff;
+  for (uint32_t k = 0; k < t->n; ++k) eff.push_back(t->info[k].r);
+  const uint64_t hp = fnv1a(eff.data(), eff.size() * 4);
+  const uint64_t hr = fnv1a(ranges, (size_t)n * sizeof(cuboid_range));
+  char buf[512];
+  std::string name(prop.name);
+  for (char& c : name)
+    if (c == ' ') c = '_';
+  snprintf(buf, sizeof(buf), "%s|%016llx|%016llx|%u|%u", name.c_str(), (unsigned long long)hp,
+           (unsigned long long)hr, n, mode);
+  return buf;
+}
+
+bool cache_lookup(const char* path, const std::string& key, cuboid_tuning* tu, float* ms) {
+  if (!path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[1024];
+  bool found = false;
+  while (fgets(line, sizeof(line), f)) {
+    char k[512];
+    cuboid_tuning x{};
+    float m = 0.f;
+    if (sscanf(line, "%511s %u %u %u %u %u %f", k, &x.block_threads, &x.ctas_per_sm, &x.smem_primes,
+               &x.tiles_per_warp, &x.hot_primes, &m) == 7 &&
+        key == k) {
+      *tu = x;  // the last matching line wins
+      *ms = m;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void cache_store(const char* path, const std::string& key, const cuboid_tuning& tu, float ms) {
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %u %u %u %u %u %.6f\n", key.c_str(), tu.block_threads, tu.ctas_per_sm, tu.smem_primes,
+          tu.tiles_per_warp, tu.hot_primes, ms);
+  fclose(f);
+}
+
+struct Outcome {
+  std::vector<unsigned long long> counts, npairs;
+  unsigned long long n_surv = 0, n_roots = 0;
+  bool operator==(const Outcome& o) const {
+    return counts == o.counts && npairs == o.npairs && n_surv == o.n_surv && n_roots == o.n_roots;
+  }
+};
+
+}  // namespace
+
+// Device buffers of a result object that the tuner reads back (declared in runtime.cu).
+namespace cuboid {
+int result_snapshot(cuboid_result* r, std::vector<unsigned long long>& counts,
+                    std::vector<unsigned long long>& npairs, unsigned long long& n_surv,
+                    unsigned long long& n_roots);
+}
+
+extern "C" int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uint32_t n, uint32_t mode,
+                               void* stream, const char* cache_path, cuboid_tuning* best_out, float* best_ms) {
+  if (!t) return CUBOID_ENOTABLES;
+  if (!ranges || n == 0 || (mode & ~0xFu) || mode > CUBOID_MODE_BATCHED) return CUBOID_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const std::string key = cache_key(t, ranges, n, mode);
+  cuboid_tuning cached{};
+  float cached_ms = 0.f;
+  if (cache_lookup(cache_path, key, &cached, &cached_ms)) {
+    t->tuning = cached;
+    if (best_out) *best_out = cached;
+    if (best_ms) *best_ms = cached_ms;
+    return CUBOID_OK;
+  }
+  cuboid_result* res = nullptr;
+  int st = result_create(t, n, 0, 0, &res);
+  if (st != CUBOID_OK) return st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const cuboid_tuning saved = t->tuning;
+
+  Outcome ref;
+  bool have_ref = false;
+  bool mismatch = false;
+  auto measure = [&](const cuboid_tuning& tu, float* out_ms) -> int {
+    t->tuning = tu;
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, s);
+      int r2 = sieve_into(res, ranges, n, mode, s, false, false);
+      if (r2 != CUBOID_OK) return r2;
+      cudaEventRecord(e1, s);
+      const int w = result_wait(res);
+      if (w != CUBOID_OK && w != CUBOID_EOVERFLOW) return w;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best = std::min(best, ms);
+    }
+    Outcome o;
+    result_snapshot(res, o.counts, o.npairs, o.n_surv, o.n_roots);
+    if (!have_ref) {
+      ref = o;
+      have_ref = true;
+    } else if (!(o == ref)) {
+      mismatch = true;
+    }
+    *out_ms = best;
+    return CUBOID_OK;
+  };
+
+  int sms = t->sms;
+  (void)sms;
+  cuboid_tuning cur{512, 2, 0, 3, 5, 0};
+  float cur_ms = 0.f;
+  st = measure(cur, &cur_ms);
+  const uint32_t hots[] = {2, 4, 5, 6, 8};
+  const uint32_t tpws[] = {1, 2, 3, 4, 6, 8, 12, 16};
+  const uint32_t thr[] = {256, 512};
+  const uint32_t ctas[] = {1, 2, 4};
+  const uint32_t smemp[] = {0, 8, 16, 32};
+  for (int pass = 0; pass < 2 && st == CUBOID_OK && !mismatch; ++pass) {
+    auto try_dim = [&](auto setter, const uint32_t* vals, int nv) {
+      for (int i = 0; i < nv && st == CUBOID_OK && !mismatch; ++i) {
+        cuboid_tuning c = cur;
+        setter(c, vals[i]);
+        if (c.block_threads * c.ctas_per_sm > 2048) continue;
+        if (std::memcmp(&c, &cur, sizeof(c)) == 0) continue;
+        float ms = 0.f;
+        st = measure(c, &ms);
+        if (st == CUBOID_OK && ms < cur_ms) {
+          cur = c;
+          cur_ms = ms;
+        }
+      }
+    };
+    try_dim([](cuboid_tuning& c, uint32_t v) { c.hot_primes = v; }, hots, 5);
+    try_dim([](cuboid_tuning& c, uint32_t v) { c.tiles_per_warp = v; }, tpws, 8);
+    try_dim([](cuboid_tuning& c, uint32_t v) { c.block_threads = v; }, thr, 2);
+    try_dim([](cuboid_tuning& c, uint32_t v) { c.ctas_per_sm = v; }, ctas, 3);
+    try_dim([](cuboid_tuning& c, uint32_t v) { c.smem_primes = v; }, smemp, 4);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cuboid_result_free(res);
+  if (st != CUBOID_OK) {
+    t->tuning = saved;
+    return st;
+  }
+  if (mismatch) {
+    t->tuning = saved;
+    return CUBOID_EVERIFY;
+  }
+  t->tuning = cur;
+  cache_store(cache_path, key, cur, cur_ms);
+  if (best_out) *best_out = cur;
+  if (best_ms) *best_ms = cur_ms;
+  return CUBOID_OK;
+}
