@@ -261,6 +261,17 @@ int cuboid_sieve_noalloc(const cuboid_tables* t, const cuboid_range* ranges_dev,
                          uint32_t* root_range_dev, uint64_t root_cap, uint64_t* totals_dev,
                          void* stream);
 
+/* ================================================================ sharding */
+
+/* Shard i of k (0 <= i < k) of range r for k GPUs or processes: contiguous blocks of rows
+ * holding about 1/k of the range's lattice points each (rows of p for CUBOID_Q_LT_P
+ * triangles; rows of the longer side for rectangles).  The shards partition the range:
+ * their sieve results add up (counts, pair totals) and concatenate (survivors, roots) to
+ * the whole range's.  *out gets the shard (p_lo > p_hi or q_lo > q_hi when it is empty);
+ * *points (may be NULL) its lattice-point count before coprimality.  Host only, no CUDA
+ * call.  Errors: EINVAL (NULL, k = 0, i >= k), ERANGE (invalid r). */
+int cuboid_shard_range(const cuboid_range* r, uint32_t k, uint32_t i, cuboid_range* out, uint64_t* points);
+
 /* ================================================================ exact root test */
 
 /* Run the exact integer-root test on n arbitrary (p, q) pairs (host arrays, p, q >= 1),

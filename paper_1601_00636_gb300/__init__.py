@@ -94,6 +94,8 @@ _SIGS = {
     "cuboid_result_stats": (C.c_int, [_P, C.POINTER(cuboid_stats)]),
     "cuboid_result_free": (C.c_int, [_P]),
     "cuboid_sieve_noalloc": (C.c_int, [_P, _P, _u32, _P, _P, _P, _P, _u64, _P, _P, _u64, _P, _P]),
+    "cuboid_shard_range": (C.c_int, [C.POINTER(cuboid_range), _u32, _u32, C.POINTER(cuboid_range),
+                                     C.POINTER(_u64)]),
     "cuboid_verify_pairs": (C.c_int, [C.POINTER(_u32), C.POINTER(_u32), _u32, _P, C.POINTER(cuboid_root),
                                       _u64, C.POINTER(_u64)]),
     "cuboid_server_create": (C.c_int, [_P, _u64, _u32, C.POINTER(_P)]),
@@ -289,6 +291,19 @@ def cuboid_sieve_noalloc(t, ranges_dev_ptr: int, n: int, counts_dev_ptr: int, np
     return _lib.cuboid_sieve_noalloc(t, ranges_dev_ptr, n, counts_dev_ptr, npairs_dev_ptr, surv_dev_ptr,
                                      surv_range_dev_ptr, surv_cap, roots_dev_ptr, root_range_dev_ptr,
                                      root_cap, totals_dev_ptr, _stream(stream))
+
+
+def cuboid_shard_range(rng, k: int, i: int):
+    """Shard i of k of a range (dict or cuboid_range): (range dict or None if empty, points)."""
+    r = rng if isinstance(rng, cuboid_range) else range_from_dict(rng)
+    out = cuboid_range()
+    pts = _u64()
+    _check(_lib.cuboid_shard_range(C.byref(r), k, i, C.byref(out), C.byref(pts)), "cuboid_shard_range")
+    if out.p_lo > out.p_hi or out.q_lo > out.q_hi:
+        return None, 0
+    return {"p_lo": out.p_lo, "p_hi": out.p_hi, "q_lo": out.q_lo, "q_hi": out.q_hi,
+            "q_lt_p": bool(out.flags & Q_LT_P), "allow_diagonal": bool(out.flags & ALLOW_DIAGONAL),
+            "flags": out.flags & (ROWS_P | ROWS_Q)}, pts.value
 
 
 def cuboid_verify_pairs(ps, qs, stream=None, cap: int | None = None):

@@ -622,6 +622,77 @@ extern "C" int cuboid_verify_pairs(const uint32_t* p, const uint32_t* q, uint32_
   return CUBOID_OK;
 }
 
+// ------------------------------------------------------------------ sharding
+
+namespace {
+
+typedef unsigned __int128 u128;
+
+// Lattice points of the triangle rows x = p_lo..p (p >= p_lo - 1): row x holds the q in
+// [q_lo, min(q_hi, x - 1 + diag)].
+u128 tri_points(const cuboid_range& R, uint64_t p) {
+  const int64_t diag = (R.flags & CUBOID_ALLOW_DIAGONAL) ? 1 : 0;
+  const int64_t W = (int64_t)R.q_hi - R.q_lo + 1;
+  const int64_t z = (int64_t)R.q_lo - diag;  // row x holds min(W, max(0, x - z)) points
+  auto F = [&](int64_t x) -> u128 {           // sum over rows <= x
+    if (x <= z) return 0;
+    const int64_t k = x - z;
+    if (k <= W) return (u128)k * (u128)(k + 1) / 2;
+    return (u128)W * (u128)(W + 1) / 2 + (u128)(k - W) * (u128)W;
+  };
+  return F((int64_t)p) - F((int64_t)R.p_lo - 1);
+}
+
+}  // namespace
+
+extern "C" int cuboid_shard_range(const cuboid_range* r, uint32_t k, uint32_t i, cuboid_range* out,
+                                  uint64_t* points) {
+  if (!r || !out || k == 0 || i >= k) return CUBOID_EINVAL;
+  const cuboid_range R = *r;
+  if (validate_ranges(&R, 1) != CUBOID_OK) return CUBOID_ERANGE;
+  cuboid_range S = R;
+  if (R.flags & CUBOID_Q_LT_P) {
+    const u128 total = tri_points(R, R.p_hi);
+    auto cut = [&](uint32_t j) -> uint64_t {  // first row of shard j
+      if (j == 0) return R.p_lo;
+      if (j == k) return (uint64_t)R.p_hi + 1;
+      const u128 want = total * j / k;
+      uint64_t lo = R.p_lo, hi = (uint64_t)R.p_hi + 1;  // smallest p with points(p_lo..p-1) >= want
+      while (lo < hi) {
+        const uint64_t mid = (lo + hi) / 2;
+        if (tri_points(R, mid - 1) >= want) hi = mid; else lo = mid + 1;
+      }
+      return lo;
+    };
+    const uint64_t a = cut(i), b = cut(i + 1);
+    if (a >= b) {
+      S.p_lo = 1;
+      S.p_hi = 0;
+    } else {
+      S.p_lo = (uint32_t)a;
+      S.p_hi = (uint32_t)(b - 1);
+    }
+    if (points) *points = a < b ? (uint64_t)(tri_points(R, b - 1) - tri_points(R, a - 1)) : 0;
+  } else {
+    const bool along_p = (uint64_t)(R.p_hi - R.p_lo) >= (uint64_t)(R.q_hi - R.q_lo);
+    const uint64_t lo = along_p ? R.p_lo : R.q_lo, n = (uint64_t)(along_p ? R.p_hi - R.p_lo : R.q_hi - R.q_lo) + 1;
+    const uint64_t a = lo + n * i / k, b = lo + n * (i + 1) / k;  // rows [a, b)
+    const uint64_t other = (uint64_t)(along_p ? R.q_hi - R.q_lo : R.p_hi - R.p_lo) + 1;
+    uint32_t& slo = along_p ? S.p_lo : S.q_lo;
+    uint32_t& shi = along_p ? S.p_hi : S.q_hi;
+    if (a >= b) {
+      slo = 1;
+      shi = 0;
+    } else {
+      slo = (uint32_t)a;
+      shi = (uint32_t)(b - 1);
+    }
+    if (points) *points = (b - a) * other;
+  }
+  *out = S;
+  return CUBOID_OK;
+}
+
 // ------------------------------------------------------------------ measurement helpers
 
 namespace {
