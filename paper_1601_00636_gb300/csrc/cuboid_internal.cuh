@@ -105,6 +105,8 @@ struct SieveArgs {
   uint32_t range_count;         // UINT32_MAX: read hdr->n_ranges
   uint32_t n_hot;               // hot primes (0, 2, 4, 5, 6 or 8): the first n_hot of the effective order
   uint32_t hot_r[8], hot_magic[8], hot_off[8], hot_W[8];
+  uint32_t hot_step[8];
+  uint32_t n_sms;               // SMs of the device (picks the register budget of the variant)         // 2048 mod r: a lane's next word starts 32 x 64 values further on
 };
 constexpr uint32_t kMaxHot = 8;
 

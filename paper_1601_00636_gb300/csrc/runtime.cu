@@ -93,7 +93,7 @@ LaunchShape launch_shape(const cuboid_tables* t) {
   uint32_t hot = T.hot_primes ? T.hot_primes : kDefaultHot;
   if (hot > k) hot = k;
   if (hot > kMaxHot) hot = kMaxHot;
-  static const uint32_t kInst[] = {8, 6, 5, 4, 2, 0};
+  static const uint32_t kInst[] = {6, 5, 4, 2, 0};
   for (uint32_t c : kInst)
     if (c <= hot) {
       L.n_hot = c;
@@ -108,12 +108,14 @@ LaunchShape launch_shape(const cuboid_tables* t) {
 
 void fill_hot(SieveArgs& a, const cuboid_tables* t, const LaunchShape& L) {
   a.n_hot = L.n_hot;
+  a.n_sms = (uint32_t)t->sms;
   for (uint32_t h = 0; h < kMaxHot; ++h) {
     const PrimeInfo pi = h < L.n_hot ? t->info[h] : PrimeInfo{1u, 0u, 0u, 0u};
     a.hot_r[h] = pi.r;
     a.hot_magic[h] = pi.magic;
     a.hot_off[h] = pi.off;
     a.hot_W[h] = pi.W;
+    a.hot_step[h] = 2048u % pi.r;
   }
 }
 

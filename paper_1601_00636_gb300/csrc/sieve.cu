@@ -299,8 +299,10 @@ __device__ __forceinline__ void drain(const SieveArgs& a, const PrimeInfo* s_inf
 
 // K: number of "hot" primes (the first K of the effective order, all resident in shared
 // memory).
-template <bool kSteps, int K>
-__global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
+// kMaxThreads: 1024 keeps every kernel at <= 64 registers (two 512-thread CTAs per SM);
+// 512 lets a single 512-thread CTA per SM use up to 128 registers.
+template <bool kSteps, int K, int kMaxThreads>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   extern __shared__ uint4 smem_raw[];
   const uint32_t n = a.n_primes;
   const uint32_t warps = blockDim.x >> 5;
@@ -353,6 +355,8 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
   unsigned long long next = 0;
   if (lane == 0) next = atomicAdd(&a.hdr->cursor, 1ull);
   next = __shfl_sync(FULL, next, 0);
+  TilePlan P1{};  // a single-range launch reads its plan once
+  if (count == 1) P1 = a.plan[a.range_first];
 
   for (;;) {
     const unsigned long long tile = next;
@@ -368,7 +372,7 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
       }
       k = lo;
     }
-    const TilePlan P = a.plan[k];
+    const TilePlan P = count == 1 ? P1 : a.plan[k];
     const unsigned long long tbeg = (k == a.range_first) ? 0ull : a.plan[k - 1].tile_end;
     if (k != ws.cur_range || ws.tiles_since_flush >= kFlushTiles) {
       drain<kSteps>(a, s_info, s_tab, wcnt, s_queue, qn, K, q_rows, ws.cur_range, lane, ws, st_wsteps,
@@ -457,6 +461,8 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
           s_fac[nfo] = make_uint4(m, kLaneStride % m, m < 64 ? s_foff[m] : kBitTab, m < 64 ? m - 1 : 64u);
         ++nfo;
       }
+      // inert entries up to kFacRegs: offset 64 that never moves, empty mask
+      if (lane < (uint32_t)kFacRegs && lane >= nfo) s_fac[lane] = make_uint4(1u, 0u, kBitTab, 64u);
       __syncwarp();
     }
     // per-lane offset of the first multiple of each odd factor in the lane's first word
@@ -465,7 +471,7 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
       const uint32_t y0f = (wbeg + lane) << 6;
 #pragma unroll
       for (int i = 0; i < kFacRegs; ++i) {
-        tf[i] = 0;
+        tf[i] = 64u;  // inert entry
         if ((uint32_t)i < nfo) {
           const uint32_t f = s_fac[i].x;
           const uint32_t s = y0f % f;
@@ -476,8 +482,12 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
 
     // ---- row offsets of the hot primes
     uint32_t rb[K > 0 ? K : 1];
+    uint32_t sh[K > 0 ? K : 1];  // y0 mod r of the lane's current word, advanced per slot
 #pragma unroll
-    for (int h = 0; h < K; ++h) rb[h] = a.hot_off[h] + mod_min(x, a.hot_r[h], a.hot_magic[h]) * a.hot_W[h];
+    for (int h = 0; h < K; ++h) {
+      rb[h] = a.hot_off[h] + mod_min(x, a.hot_r[h], a.hot_magic[h]) * a.hot_W[h];
+      sh[h] = mod_min((wbeg + lane) << 6, a.hot_r[h], a.hot_magic[h]);
+    }
 
     uint32_t hcnt[K > 0 ? K : 1];
 #pragma unroll
@@ -496,15 +506,13 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
         al = has2 ? (rml & 0xAAAAAAAAu) : rml;  // y0 is even: even y at even bits
         ah = has2 ? (rmh & 0xAAAAAAAAu) : rmh;
 #pragma unroll
-        for (int i = 0; i < kFacRegs; ++i) {
-          if ((uint32_t)i < nfo) {
-            const uint4 fc = s_fac[i];  // {f, 2048 mod f, table base, cap}
-            const uint2 mk = s_mtab[fc.z + min(tf[i], fc.w)];
-            al &= ~mk.x;
-            ah &= ~mk.y;
-            // the lane's next word starts 2048 further on: t <- (t - 2048) mod f
-            tf[i] = tf[i] >= fc.y ? tf[i] - fc.y : tf[i] - fc.y + fc.x;
-          }
+        for (int i = 0; i < kFacRegs; ++i) {  // inert entries give an empty mask
+          const uint4 fc = s_fac[i];          // {f, 2048 mod f, table base, cap}
+          const uint2 mk = s_mtab[fc.z + min(tf[i], fc.w)];
+          al &= ~mk.x;
+          ah &= ~mk.y;
+          // the lane's next word starts 2048 further on: t <- (t - 2048) mod f
+          tf[i] = tf[i] >= fc.y ? tf[i] - fc.y : tf[i] - fc.y + fc.x;
         }
         for (uint32_t i = kFacRegs; i < nfo; ++i) {
           const uint4 fc = s_fac[i];
@@ -529,7 +537,9 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
 #pragma unroll
       for (int h = 0; h < K; ++h) {
         if (kSteps) st_wsteps += (al | ah) ? 1 : 0;
-        const uint32_t s = mod_min(y0, a.hot_r[h], a.hot_magic[h]);
+        const uint32_t s = sh[h];
+        const uint32_t sn = s + a.hot_step[h];  // next word: + 2048 mod r, below 2r
+        sh[h] = min(sn, sn - a.hot_r[h]);
         const uint32_t* tp = s_tab + rb[h] + (s >> 5);
         const uint32_t w0 = tp[0], w1 = tp[1], w2 = tp[2];
         const uint32_t rl = __funnelshift_r(w0, w1, s) & al, rh = __funnelshift_r(w1, w2, s) & ah;
@@ -575,28 +585,42 @@ __global__ void __launch_bounds__(1024) k_sieve(SieveArgs a) {
   }
 }
 
-template <bool S>
-cudaError_t set_attr_all(size_t bytes) {
+template <bool S, int M>
+cudaError_t set_attr_m(size_t bytes) {
   const int b = (int)bytes;
-  cudaError_t e = cudaFuncSetAttribute(k_sieve<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaError_t e = cudaFuncSetAttribute(k_sieve<S, 0, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 2, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 4, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 5, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 6, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   return e;
 }
 
 template <bool S>
-void launch_k(const SieveArgs& a, uint32_t blocks, uint32_t threads, size_t smem, cudaStream_t s) {
+cudaError_t set_attr_all(size_t bytes) {
+  cudaError_t e = set_attr_m<S, 1024>(bytes);
+  if (e == cudaSuccess) e = set_attr_m<S, 512>(bytes);
+  return e;
+}
+
+template <bool S, int M>
+void launch_m(const SieveArgs& a, uint32_t blocks, uint32_t threads, size_t smem, cudaStream_t s) {
   switch (a.n_hot) {
-    case 8: k_sieve<S, 8><<<blocks, threads, smem, s>>>(a); break;
-    case 6: k_sieve<S, 6><<<blocks, threads, smem, s>>>(a); break;
-    case 5: k_sieve<S, 5><<<blocks, threads, smem, s>>>(a); break;
-    case 4: k_sieve<S, 4><<<blocks, threads, smem, s>>>(a); break;
-    case 2: k_sieve<S, 2><<<blocks, threads, smem, s>>>(a); break;
-    default: k_sieve<S, 0><<<blocks, threads, smem, s>>>(a); break;
+    case 6: k_sieve<S, 6, M><<<blocks, threads, smem, s>>>(a); break;
+    case 5: k_sieve<S, 5, M><<<blocks, threads, smem, s>>>(a); break;
+    case 4: k_sieve<S, 4, M><<<blocks, threads, smem, s>>>(a); break;
+    case 2: k_sieve<S, 2, M><<<blocks, threads, smem, s>>>(a); break;
+    default: k_sieve<S, 0, M><<<blocks, threads, smem, s>>>(a); break;
   }
+}
+
+// The 128-register variant serves shapes with at most 512 threads per SM.
+template <bool S>
+void launch_k(const SieveArgs& a, uint32_t blocks, uint32_t threads, uint32_t per_sm, size_t smem, cudaStream_t s) {
+  if (threads * per_sm <= 512)
+    launch_m<S, 512>(a, blocks, threads, smem, s);
+  else
+    launch_m<S, 1024>(a, blocks, threads, smem, s);
 }
 
 }  // namespace
@@ -627,10 +651,11 @@ cudaError_t launch_plan(const cuboid_range* ranges, uint32_t first, uint32_t cou
 
 cudaError_t launch_sieve(const SieveArgs& a, bool count_steps, uint32_t blocks, uint32_t threads,
                          size_t smem, cudaStream_t s) {
+  const uint32_t per_sm = a.n_sms ? (blocks + a.n_sms - 1) / a.n_sms : 2;
   if (count_steps)
-    launch_k<true>(a, blocks, threads, smem, s);
+    launch_k<true>(a, blocks, threads, per_sm, smem, s);
   else
-    launch_k<false>(a, blocks, threads, smem, s);
+    launch_k<false>(a, blocks, threads, per_sm, smem, s);
   return cudaGetLastError();
 }
 

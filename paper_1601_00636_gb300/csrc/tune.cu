@@ -152,12 +152,10 @@ extern "C" int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uin
     return CUBOID_OK;
   };
 
-  int sms = t->sms;
-  (void)sms;
   cuboid_tuning cur{512, 2, 0, 3, 5, 0};
   float cur_ms = 0.f;
   st = measure(cur, &cur_ms);
-  const uint32_t hots[] = {2, 4, 5, 6, 8};
+  const uint32_t hots[] = {2, 4, 5, 6};
   const uint32_t tpws[] = {1, 2, 3, 4, 6, 8, 12, 16};
   const uint32_t thr[] = {256, 512};
   const uint32_t ctas[] = {1, 2, 4};
@@ -177,7 +175,7 @@ extern "C" int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uin
         }
       }
     };
-    try_dim([](cuboid_tuning& c, uint32_t v) { c.hot_primes = v; }, hots, 5);
+    try_dim([](cuboid_tuning& c, uint32_t v) { c.hot_primes = v; }, hots, 4);
     try_dim([](cuboid_tuning& c, uint32_t v) { c.tiles_per_warp = v; }, tpws, 8);
     try_dim([](cuboid_tuning& c, uint32_t v) { c.block_threads = v; }, thr, 2);
     try_dim([](cuboid_tuning& c, uint32_t v) { c.ctas_per_sm = v; }, ctas, 3);
