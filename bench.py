@@ -35,7 +35,10 @@ import workloads as W  # noqa: E402
 
 METRIC = "sieved coprime (p,q) pairs/s"
 UNIT = "pairs/s"
-OPS_PER_WORD_STEP = 10  # lane-ops of one prime test of one 32-q word (see the design notes)
+# lane-ops of one prime test of one 64-value word: residue (2), address (1), three table
+# loads (3), two funnel shifts (2), two ANDs (2), two popcounts (2), count add (1), two
+# alive updates (2)
+OPS_PER_WORD_STEP = 15
 
 
 def parse():
@@ -312,6 +315,7 @@ def run_ours(args):
     time.sleep(0.3)
     evs = []
     sieve_ms, sieve_launches = 0.0, 0
+    torch.cuda.nvtx.range_push("timed")  # profilers capture only this region
     for _ in range(args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
@@ -324,6 +328,7 @@ def run_ours(args):
         sieve_ms += ms
         sieve_launches += nl
         evs.append((a, b))
+    torch.cuda.nvtx.range_pop()
     barrier()
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in evs)

@@ -81,6 +81,8 @@ struct cuboid_tables {
   cuboid_tuning tuning{};
   std::atomic<int> users{0};        // servers holding the tables
   int sms = 0;
+  int smem_per_sm = 0;              // device limits read once at build time
+  int smem_per_block = 0;
 };
 
 namespace cuboid {

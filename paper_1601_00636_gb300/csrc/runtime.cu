@@ -70,9 +70,7 @@ LaunchShape launch_shape(const cuboid_tables* t) {
   LaunchShape L;
   L.threads = T.block_threads ? T.block_threads : kDefaultThreads;
   const uint32_t ctas = T.ctas_per_sm ? T.ctas_per_sm : kDefaultCtasPerSm;
-  int smem_sm = 0, smem_blk = 0;
-  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, t->device);
-  cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, t->device);
+  const int smem_sm = t->smem_per_sm, smem_blk = t->smem_per_block;
   const size_t fixed = sieve_smem_bytes(0, t->n, L.threads);
   size_t per_cta = std::min<size_t>((size_t)smem_blk, (size_t)smem_sm / ctas - 1024);
   size_t table_budget = per_cta > fixed ? per_cta - fixed : 0;

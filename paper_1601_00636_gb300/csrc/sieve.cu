@@ -16,6 +16,8 @@
 // compacted with a warp prefix sum and one atomic per warp.  Tiles come from a device
 // queue (one atomic per tile), so one kernel serves one range per launch and thousands
 // of ranges per launch.
+#include <mutex>
+
 #include "cuboid_internal.cuh"
 
 namespace cuboid {
@@ -632,8 +634,20 @@ size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads
          (size_t)warps * n_primes * sizeof(uint32_t) + (size_t)smem_words * sizeof(uint32_t);
 }
 
+// The dynamic shared-memory limit is a per-device function attribute: raise it only when
+// a launch needs more than what was set before (each call costs host time).
 cudaError_t sieve_set_smem_limit(bool count_steps, size_t bytes) {
-  return count_steps ? set_attr_all<true>(bytes) : set_attr_all<false>(bytes);
+  static std::mutex mu;
+  static size_t set_bytes[64][2];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return count_steps ? set_attr_all<true>(bytes) : set_attr_all<false>(bytes);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set_bytes[dev][count_steps ? 1 : 0];
+  if (bytes <= cur) return cudaSuccess;
+  const cudaError_t e = count_steps ? set_attr_all<true>(bytes) : set_attr_all<false>(bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 cudaError_t launch_reset(DevHeader* hdr, uint32_t n_ranges, cudaStream_t s) {

@@ -226,6 +226,8 @@ int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_
   t->primes = pr;
   cudaGetDevice(&t->device);
   cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device);
+  cudaDeviceGetAttribute(&t->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, t->device);
+  cudaDeviceGetAttribute(&t->smem_per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, t->device);
 
   uint32_t* d_primes = nullptr;
   unsigned long long* d_voff = nullptr;
