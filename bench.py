@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the batched/large/e2e/cpu legs")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4top"],
+                    help="c2: the 2^14 triangle (the headline); c4top: the 4097 largest rows of the "
+                         "2^20 triangle with 256 primes (the long-row regime, for profiling)")
     return ap.parse_args()
 
 
@@ -246,11 +249,14 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     cfg = W.c2()
+    if args.workload == "c4top":
+        cfg = {"name": "c4top_rows2^20-4096..2^20_256primes", "primes": W.first_odd_primes(256),
+               "ranges": [W.rect((1 << 20) - 4096, 1 << 20, 1, (1 << 20) - 1, q_lt_p=True)]}
     primes = cfg["primes"]
     rng = cfg["ranges"][0]
     n_primes = len(primes)
     whole_max = 1 << 14
-    if world > 1:
+    if world > 1 and args.workload == "c2":
         # weak scaling: the triangle grows with N (about N times the pairs of the 2^14
         # triangle) and each rank sieves one balanced shard of it
         import math
@@ -283,7 +289,18 @@ def run_ours(args):
     assert cb.cuboid_result_wait(res) == cb.OK
     got = cb.cuboid_result_get(res, 0, n_primes)
     n_pairs = got["n_pairs"]
-    if world == 1:
+    if args.workload == "c4top":
+        # every pair accounted for, and the pair total equals the sum of phi(p) over the rows
+        import numpy as np
+        hi = 1 << 20
+        phi = np.arange(hi + 1, dtype=np.int64)
+        for i in range(2, hi + 1):
+            if phi[i] == i:
+                phi[i::i] -= phi[i::i] // i
+        bit_exact = (sum(got["counts"]) + len(got["survivors"]) == n_pairs
+                     and n_pairs == int(phi[hi - 4096:hi + 1].sum()))
+        n_total = n_pairs * world  # replicas of the same rows on every rank
+    elif world == 1:
         bit_exact = (got["n_pairs"] == gold["n_pairs"] and got["counts"] == gold["counts"]
                      and [list(x) for x in got["survivors"]] == gold["survivors"]
                      and [list(x) for x in got["roots"]] == gold["roots"])
