@@ -379,3 +379,96 @@ def run(primes, ranges, by_density: bool = False, tables: Tables | None = None,
         roots = sorted((p, q, t) for (p, q) in surv for t in integer_roots(p, q))
         out.append({"n_pairs": n_pairs, "counts": counts, "survivors": surv, "roots": roots})
     return {"order": list(tables.order), "ranges": out}
+
+
+# --------------------------------------------------------------------------------------
+# The region of Theorem 1.2 and the search loop of section 5
+# --------------------------------------------------------------------------------------
+
+REGION_SLOPE = 59          # the factor 59 of Eq. 1.2 (q <= 59 p and q >= p / 59)
+REGION_CUBE_DIVISOR = 9    # the 9 of cbrt(p / 9) in Eq. 1.2
+
+
+def region_q_bounds(p: int) -> tuple[int, int]:
+    """Integer segment [q_lo, q_hi] of row p in the region of Eq. 1.2,
+    min(cbrt(p/9), p/59) <= q <= 59 p, for p >= 1.  An integer q >= 1 satisfies
+    q >= cbrt(p/9) iff 9 q^3 >= p iff q^3 >= ceil(p/9), and q >= p/59 iff q >= ceil(p/59);
+    q is at least one of them iff it is at least the smaller of the two integer bounds."""
+    q_cube = _ceil_root(-(-p // REGION_CUBE_DIVISOR), 3)
+    q_lin = -(-p // REGION_SLOPE)
+    return max(1, min(q_cube, q_lin)), REGION_SLOPE * p
+
+
+def region_rows(p_from: int, p_to: int, q_from: int = 0) -> list[dict]:
+    """One inclusive range per row p_from..p_to over its segment of Eq. 1.2 (row p_from
+    from max(q_from, q_lo) on): the rows the search of section 5 walks."""
+    out = []
+    for p in range(p_from, p_to + 1):
+        lo, hi = region_q_bounds(p)
+        if p == p_from:
+            lo = max(lo, q_from)
+        if lo <= hi:
+            out.append({"p_lo": p, "p_hi": p, "q_lo": lo, "q_hi": hi})
+    return out
+
+
+def deepest_prime(tables: Tables, counts, n_surv: int) -> tuple[int, int]:
+    """(depth, r_max): the 1-based position in the effective order of the last prime that
+    rejected some pair (every prime when a pair survived), and that prime; (0, 0) if no
+    pair was sieved.  This is the "depth" of section 6 and the r_max of section 5."""
+    depth = len(tables.order) if n_surv else 0
+    if not n_surv:
+        for e, i in enumerate(tables.order):
+            if counts[i]:
+                depth = e + 1
+    return depth, (tables.primes[tables.order[depth - 1]] if depth else 0)
+
+
+def region_scan(tables: Tables, p_from: int, p_to: int, q_from: int = 0) -> dict:
+    """The section 5 search over rows p_from..p_to of the region of Theorem 1.2: each row
+    over its segment of Eq. 1.2, sieved with the bit sieve of section 2, survivors tested
+    for integer roots.  Returns pairs, counts (caller order), survivors, roots, depth and
+    r_max over the whole scan."""
+    n = len(tables.primes)
+    counts = [0] * n
+    n_pairs = 0
+    surv: list[tuple[int, int]] = []
+    for rng in region_rows(p_from, p_to, q_from):
+        k, c, s = sieve_range(tables, rng)
+        n_pairs += k
+        counts = [a + b for a, b in zip(counts, c)]
+        surv.extend(s)
+    roots = sorted((p, q, t) for (p, q) in surv for t in integer_roots(p, q))
+    depth, r_max = deepest_prime(tables, counts, len(surv))
+    return {"pairs": n_pairs, "counts": counts, "survivors": surv, "roots": roots,
+            "depth": depth, "r_max": r_max}
+
+
+def region_pair_count(p_from: int, p_to: int) -> int:
+    """Number of coprime pairs p != q in rows p_from..p_to of the region of Eq. 1.2,
+    by Moebius inversion over the squarefree divisors d of p: the integers of [lo, hi]
+    prime to p number sum_{d | p} mu(d) (floor(hi/d) - floor((lo-1)/d)).  The pair (1, 1)
+    is coprime but diagonal and is removed."""
+    spf = list(range(p_to + 1))                      # smallest prime factor sieve
+    for i in range(2, isqrt(p_to) + 1):
+        if spf[i] == i:
+            for j in range(i * i, p_to + 1, i):
+                if spf[j] == j:
+                    spf[j] = i
+    total = 0
+    for p in range(p_from, p_to + 1):
+        lo, hi = region_q_bounds(p)
+        rad = []
+        m = p
+        while m > 1:
+            f = spf[m]
+            rad.append(f)
+            while m % f == 0:
+                m //= f
+        divs = [(1, 1)]
+        for f in rad:
+            divs += [(d * f, -s) for (d, s) in divs]
+        total += sum(s * (hi // d - (lo - 1) // d) for (d, s) in divs)
+        if lo <= p <= hi and p == 1:
+            total -= 1
+    return total

@@ -356,3 +356,81 @@ def test_ceil_root_exact():
     for k in (2, 3, 5):
         for b in (1, 2, 10 ** 40 + 1):
             assert _ceil_root(b ** k, k) == b
+
+
+# ---------------------------------------------------------------- region of Theorem 1.2
+
+def _smallest_q(pred):
+    q = 1
+    while not pred(q):
+        q += 1
+    return q
+
+
+def test_region_bounds_follow_eq_5_1_and_5_2():
+    """Eq. 5.1 (p <= 151: p/59 <= q) and Eq. 5.2 (p >= 152: cbrt(p/9) <= q) are the two
+    cases of the min() of Eq. 1.2; found here by brute force with exact rationals (the
+    cube root compared by cubing), independently of the oracle's integer bounds."""
+    from fractions import Fraction as F
+    for p in list(range(1, 1200)) + [5000, 12345, 154000, 72796055]:
+        linear_is_min = F(p, 59) ** 3 <= F(p, 9)
+        assert linear_is_min == (p <= 151)
+        if p <= 151:
+            lo = _smallest_q(lambda q: F(q) >= F(p, 59))
+        else:
+            lo = _smallest_q(lambda q: F(q) ** 3 >= F(p, 9))
+        assert O.region_q_bounds(p) == (lo, 59 * p)
+
+
+def test_region_start_and_stop_examples():
+    """Section 5: the search starts at (152, 3), whose q obeys Eq. 5.2 and is the first
+    such q; the printed stop point (112618, 5691455) lies inside its row's segment; p_max
+    = 72796055 is the last p with 59 p below 2^32."""
+    assert O.region_q_bounds(152)[0] == 3
+    lo, hi = O.region_q_bounds(112618)
+    assert lo <= 5691455 <= hi
+    assert 59 * 72796055 < 2 ** 32 <= 59 * 72796056
+
+
+def test_region_pair_count_brute_force():
+    """The Moebius count of coprime pairs equals enumeration on small row blocks."""
+    for a, b in [(1, 60), (140, 165), (997, 1003)]:
+        brute = sum(len(O.row_pairs(r["p_lo"], r)) for r in O.region_rows(a, b))
+        assert O.region_pair_count(a, b) == brute
+
+
+def test_region_pair_count_section6():
+    """Section 6 counts about sum_{p <= 154000} 59 p = 699626543000 lattice points; the
+    coprime pairs among them are close to 6/pi^2 of that."""
+    n_lattice = sum(59 * p for p in range(1, 154001))
+    assert n_lattice == 699626543000
+    exact = sum(hi - lo + 1 for lo, hi in map(O.region_q_bounds, range(1, 154001)))
+    assert abs(exact - n_lattice) / n_lattice < 1e-4
+    coprime = O.region_pair_count(1, 154000)
+    assert abs(coprime / exact - 6 / math.pi ** 2) < 1e-3
+
+
+def test_region_scan_matches_pairwise():
+    """The region scan (numpy rows) equals the one-pair-at-a-time sieve over the same
+    rows, from a mid-row start, with survivors (few primes)."""
+    T = O.Tables([3, 5, 7, 11, 13], full_limit=0)
+    got = O.region_scan(T, 20, 26, q_from=40)
+    counts = [0] * 5
+    surv, pairs = [], 0
+    for rng in O.region_rows(20, 26, 40):
+        k, c, s = O.sieve_range_pairwise(T, rng)
+        pairs += k
+        counts = [x + y for x, y in zip(counts, c)]
+        surv += s
+    assert (got["pairs"], got["counts"], got["survivors"]) == (pairs, counts, surv)
+    assert surv and got["depth"] == 5 and got["r_max"] == T.primes[T.order[-1]]
+    assert O.region_rows(150, 152, 40)[0]["q_lo"] == 40
+    assert [r["q_lo"] for r in O.region_rows(150, 152, 40)[1:]] == [3, 3]
+
+
+def test_deepest_prime():
+    """Depth is the position of the last nonzero count in the effective order."""
+    T = O.Tables([11, 13, 17, 19], full_limit=0)
+    assert O.deepest_prime(T, [5, 0, 2, 0], 0) == (3, 17)
+    assert O.deepest_prime(T, [0, 0, 0, 0], 0) == (0, 0)
+    assert O.deepest_prime(T, [1, 0, 0, 0], 3) == (4, 19)
