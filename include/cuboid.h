@@ -39,7 +39,10 @@ extern "C" {
  * (section 5): 0 success, 1 busy, 2..5 out-of-range start values, 6 tables missing. */
 #define CUBOID_OK          0
 #define CUBOID_EBUSY       1  /* object in use (tables held by a server; no free slot) */
-#define CUBOID_ERANGE      2  /* a bound is 0, lo > hi, or p, q outside 32 bits */
+#define CUBOID_ERANGE      2  /* a bound is 0, lo > hi, or p, q outside 32 bits; search: p < 152 */
+#define CUBOID_EPMAX       3  /* search: p > 72796055, so 59 p leaves 32 bits (section 5) */
+#define CUBOID_EQLOW       4  /* search: q below the region of Eq. 5.2 */
+#define CUBOID_EQHIGH      5  /* search: q above 59 p (Eq. 5.2) */
 #define CUBOID_ENOTABLES   6  /* NULL tables handle */
 #define CUBOID_EINVAL      7  /* invalid argument (NULL pointer, bad prime list, ...) */
 #define CUBOID_ENOMEM      8  /* device or pinned allocation failed */
@@ -260,6 +263,64 @@ int cuboid_sieve_noalloc(const cuboid_tables* t, const cuboid_range* ranges_dev,
                          uint32_t* surv_range_dev, uint64_t surv_cap, cuboid_root* roots_dev,
                          uint32_t* root_range_dev, uint64_t root_cap, uint64_t* totals_dev,
                          void* stream);
+
+/* ================================================================ region search (section 5) */
+
+/* The region of Theorem 1.2 (Eq. 1.2): min(cbrt(p/9), p/59) <= q <= 59 p; for p >= 152
+ * it is the segment of Eq. 5.2, cbrt(p/9) <= q <= 59 p.  A scan walks the rows p upward,
+ * each row over its segment, in batches of 100 rows (the granularity of the paper's
+ * Get_current_p), sieving coprime q != p. */
+typedef struct cuboid_search_report {
+  uint32_t p, q;      /* where a resumed scan starts: the next row and its first q */
+  uint32_t r_max;     /* deepest prime needed (last rejecting prime in the effective order
+                         over the scanned rows; every prime if a pair survived); 0 if none */
+  uint32_t depth;     /* its 1-based position in the effective order */
+  uint64_t pairs;     /* coprime pairs sieved */
+  uint64_t n_surv;    /* pairs that passed every prime */
+  uint64_t n_roots;   /* integer roots found on them */
+} cuboid_search_report;
+
+/* Smallest q of row p in the region of Eq. 1.2 (>= 1). */
+uint32_t cuboid_region_qmin(uint32_t p);
+
+/* Synchronous scan of rows p_from..p_to (row p_from from q_from on; q_from = 0: its
+ * segment start).  counts (n_primes, caller order, may be NULL) receives the per-prime
+ * first-rejecter counts, surv / roots (capacities surv_cap / root_cap, may be NULL with
+ * cap 0) the survivor and root records in scan order, rep the report.  Any p_from >= 1
+ * is accepted (rows below 152 use the min() of Eq. 1.2).  Synchronous on stream.
+ * Errors: ENOTABLES; ERANGE if p_from = 0 or p_to < p_from; EPMAX if p_to > 72796055;
+ * EQLOW / EQHIGH if q_from (when nonzero) lies outside row p_from's segment; EOVERFLOW if
+ * more survivors or roots arrived than a buffer holds (the per-prime counts and the pair
+ * and survivor totals stay exact; records and roots past a capacity are dropped). */
+int cuboid_region_scan(cuboid_tables* t, uint32_t p_from, uint32_t q_from, uint32_t p_to, void* stream,
+                       uint64_t* counts, uint64_t* surv, uint64_t surv_cap, cuboid_root* roots,
+                       uint64_t root_cap, cuboid_search_report* rep);
+
+typedef struct cuboid_search cuboid_search;
+
+/* Start an open-ended scan at row p, column q on a host thread and return at once
+ * (the paper's Start_searching, section 5).  Codes as the paper's: 0 started;
+ * CUBOID_EBUSY (1) a search already runs on these tables; CUBOID_ERANGE (2) p < 152;
+ * CUBOID_EPMAX (3) p > 72796055; CUBOID_EQLOW (4) q below the segment of Eq. 5.2;
+ * CUBOID_EQHIGH (5) q > 59 p; CUBOID_ENOTABLES (6) no tables.  The tables stay in use
+ * (cuboid_tables_free returns EBUSY) until cuboid_search_stop. */
+int cuboid_search_start(cuboid_tables* t, uint32_t p, uint32_t q, cuboid_search** out);
+
+/* Progress (the paper's Get_current_p and Get_current_r_max): the first row of the
+ * batch of 100 rows being scanned, and the deepest prime needed within it. */
+int cuboid_search_current(const cuboid_search* s, uint32_t* p, uint32_t* r_max);
+
+/* Stop after the batch in flight (the paper's Stop_searching), fill the report (p, q of
+ * the next row: pass them to cuboid_search_start to resume), the totals and counts
+ * (n_primes, caller order, may be NULL), and free the handle.  Survivor and root records
+ * are not kept by a search (their numbers are in the report; cuboid_region_scan returns
+ * records).  Returns the first error the scan met, else 0; EINVAL (NULL handle). */
+int cuboid_search_stop(cuboid_search* s, cuboid_search_report* rep, uint64_t* counts);
+
+/* Append the report to a text file in the paper's form (section 5): a local time stamp
+ * line "Y-M-D HH:MM" and "Stop with p=<p>, q=<q>, r_max=<r_max>".  Host only.
+ * Errors: EINVAL (NULL argument, file not writable). */
+int cuboid_search_report_write(const cuboid_search_report* rep, const char* path);
 
 /* ================================================================ sharding */
 

@@ -23,10 +23,10 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 # ------------------------------------------------------------------ constants (cuboid.h)
-OK, EBUSY, ERANGE, ENOTABLES, EINVAL, ENOMEM = 0, 1, 2, 6, 7, 8
+OK, EBUSY, ERANGE, EPMAX, EQLOW, EQHIGH, ENOTABLES, EINVAL, ENOMEM = 0, 1, 2, 3, 4, 5, 6, 7, 8
 ETIMEOUT, ECUDA, EOVERFLOW, EAGAIN, EVERIFY, ETOOLARGE = 9, 10, 11, 12, 13, 14
 NOALLOC_MAX_RANGES = 4096
-STATUS_NAMES = {0: "OK", 1: "EBUSY", 2: "ERANGE", 6: "ENOTABLES", 7: "EINVAL", 8: "ENOMEM",
+STATUS_NAMES = {0: "OK", 1: "EBUSY", 2: "ERANGE", 3: "EPMAX", 4: "EQLOW", 5: "EQHIGH", 6: "ENOTABLES", 7: "EINVAL", 8: "ENOMEM",
                 9: "ETIMEOUT", 10: "ECUDA", 11: "EOVERFLOW", 12: "EAGAIN", 13: "EVERIFY", 14: "ETOOLARGE"}
 
 ORDER_AS_GIVEN, ORDER_BY_DENSITY, ORDER_BY_RATE = 0x0, 0x1, 0x4
@@ -67,6 +67,11 @@ class cuboid_stats(C.Structure):
                 ("tiles", C.c_uint64)]
 
 
+class cuboid_search_report(C.Structure):
+    _fields_ = [("p", C.c_uint32), ("q", C.c_uint32), ("r_max", C.c_uint32), ("depth", C.c_uint32),
+                ("pairs", C.c_uint64), ("n_surv", C.c_uint64), ("n_roots", C.c_uint64)]
+
+
 _P = C.c_void_p
 _u32, _u64 = C.c_uint32, C.c_uint64
 _SIGS = {
@@ -94,6 +99,13 @@ _SIGS = {
     "cuboid_result_stats": (C.c_int, [_P, C.POINTER(cuboid_stats)]),
     "cuboid_result_free": (C.c_int, [_P]),
     "cuboid_sieve_noalloc": (C.c_int, [_P, _P, _u32, _P, _P, _P, _P, _u64, _P, _P, _u64, _P, _P]),
+    "cuboid_region_qmin": (_u32, [_u32]),
+    "cuboid_region_scan": (C.c_int, [_P, _u32, _u32, _u32, _P, C.POINTER(_u64), C.POINTER(_u64), _u64,
+                                     C.POINTER(cuboid_root), _u64, C.POINTER(cuboid_search_report)]),
+    "cuboid_search_start": (C.c_int, [_P, _u32, _u32, C.POINTER(_P)]),
+    "cuboid_search_current": (C.c_int, [_P, C.POINTER(_u32), C.POINTER(_u32)]),
+    "cuboid_search_stop": (C.c_int, [_P, C.POINTER(cuboid_search_report), C.POINTER(_u64)]),
+    "cuboid_search_report_write": (C.c_int, [C.POINTER(cuboid_search_report), C.c_char_p]),
     "cuboid_shard_range": (C.c_int, [C.POINTER(cuboid_range), _u32, _u32, C.POINTER(cuboid_range),
                                      C.POINTER(_u64)]),
     "cuboid_verify_pairs": (C.c_int, [C.POINTER(_u32), C.POINTER(_u32), _u32, _P, C.POINTER(cuboid_root),
@@ -291,6 +303,71 @@ def cuboid_sieve_noalloc(t, ranges_dev_ptr: int, n: int, counts_dev_ptr: int, np
     return _lib.cuboid_sieve_noalloc(t, ranges_dev_ptr, n, counts_dev_ptr, npairs_dev_ptr, surv_dev_ptr,
                                      surv_range_dev_ptr, surv_cap, roots_dev_ptr, root_range_dev_ptr,
                                      root_cap, totals_dev_ptr, _stream(stream))
+
+
+# ------------------------------------------------------------------ region search (section 5)
+
+def _report(rep: cuboid_search_report) -> dict:
+    return {k: getattr(rep, k) for k, _ in cuboid_search_report._fields_}
+
+
+def cuboid_region_qmin(p: int) -> int:
+    return int(_lib.cuboid_region_qmin(p))
+
+
+def cuboid_region_scan(t, p_from: int, p_to: int, q_from: int = 0, stream=None,
+                       surv_cap: int = 1 << 16, root_cap: int = 1 << 12):
+    """Scan rows p_from..p_to of the region.  Returns (status, report dict, counts in caller
+    order, survivor (p, q) list, root (p, q, t) list); status is OK or EOVERFLOW, others raise."""
+    n = cuboid_tables_info(t)[0]
+    counts = (_u64 * n)()
+    surv = (_u64 * max(surv_cap, 1))()
+    roots = (cuboid_root * max(root_cap, 1))()
+    rep = cuboid_search_report()
+    st = _lib.cuboid_region_scan(t, p_from, q_from, p_to, _stream(stream), counts, surv, surv_cap, roots,
+                                 root_cap, C.byref(rep))
+    if st not in (OK, EOVERFLOW):
+        _check(st, "cuboid_region_scan")
+    d = _report(rep)
+    ns, nr = min(d["n_surv"], surv_cap), min(d["n_roots"], root_cap)
+    sv = [(int(surv[i]) >> 32, int(surv[i]) & 0xFFFFFFFF) for i in range(ns)]
+    rv = [(roots[i].p, roots[i].q, (int(roots[i].t_hi) << 64) | int(roots[i].t_lo)) for i in range(nr)]
+    return st, d, list(counts), sv, rv
+
+
+def cuboid_search_start(t, p: int, q: int) -> int:
+    """Start the asynchronous search (raises CuboidError with the paper's codes 1..6)."""
+    out = _P()
+    _check(_lib.cuboid_search_start(t, p, q, C.byref(out)), "cuboid_search_start")
+    return out.value
+
+
+def cuboid_search_start_status(t, p: int, q: int):
+    """As cuboid_search_start, returning (status, handle or None) instead of raising."""
+    out = _P()
+    st = _lib.cuboid_search_start(t, p, q, C.byref(out))
+    return st, (out.value if st == OK else None)
+
+
+def cuboid_search_current(s):
+    """(first row of the batch being scanned, deepest prime needed within it)."""
+    p, r = _u32(), _u32()
+    _check(_lib.cuboid_search_current(s, C.byref(p), C.byref(r)), "cuboid_search_current")
+    return p.value, r.value
+
+
+def cuboid_search_stop(s, n_primes: int):
+    """Stop and free the search; returns (status of the scan, report dict, counts)."""
+    rep = cuboid_search_report()
+    counts = (_u64 * n_primes)()
+    st = _lib.cuboid_search_stop(s, C.byref(rep), counts)
+    return st, _report(rep), list(counts)
+
+
+def cuboid_search_report_write(rep: dict, path: str) -> None:
+    """Append a report (dict from cuboid_search_stop / cuboid_region_scan) to a text file."""
+    r = cuboid_search_report(**rep)
+    _check(_lib.cuboid_search_report_write(C.byref(r), path.encode()), "cuboid_search_report_write")
 
 
 def cuboid_shard_range(rng, k: int, i: int):

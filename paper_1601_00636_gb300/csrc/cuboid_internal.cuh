@@ -79,7 +79,8 @@ struct cuboid_tables {
   cuboid::TrialPrime* d_trial = nullptr;
   uint32_t n_trial = 0;
   cuboid_tuning tuning{};
-  std::atomic<int> users{0};        // servers holding the tables
+  std::atomic<int> users{0};        // servers and searches holding the tables
+  bool searching = false;           // a region search runs on these tables
   int sms = 0;
   int smem_per_sm = 0;              // device limits read once at build time
   int smem_per_block = 0;

@@ -16,7 +16,7 @@ def _declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:int|const char\*|void)\s+(cuboid_\w+)\s*\(", text, flags=re.M):
+        for m in re.finditer(r"^\s*(?:int|uint32_t|const char\*|void)\s+(cuboid_\w+)\s*\(", text, flags=re.M):
             names.add(m.group(1))
     return names
 
