@@ -472,3 +472,50 @@ def region_pair_count(p_from: int, p_to: int) -> int:
         if lo <= p <= hi and p == 1:
             total -= 1
     return total
+
+
+# --------------------------------------------------------------------------------------
+# The paper's table files (section 2, section 3)
+# --------------------------------------------------------------------------------------
+
+PRIMES_RECORD = "<hxxI"    # C struct {short prime; unsigned int offset;}: 8 bytes, 2 padding
+
+
+def full_table(r: int) -> np.ndarray:
+    """u_r by Definition 1.1 for r <= FULL_TABLE_LIMIT, else from v_r by homogeneity."""
+    return unsolvable_table(r) if r <= FULL_TABLE_LIMIT else full_from_reduced(r, reduced_table(r))
+
+
+def paper_table_files(primes) -> tuple[bytes, bytes]:
+    """(bit tables file, primes file) for the primes in the given order: the Eq. 2.6
+    bytes of each u_r back to back, and per prime the record (r, byte offset)."""
+    import struct
+    blob, recs = bytearray(), bytearray()
+    for r in primes:
+        recs += struct.pack(PRIMES_RECORD, r, len(blob))
+        blob += pack_table_bytes(full_table(r))
+    return bytes(blob), bytes(recs)
+
+
+def read_paper_table_files(blob: bytes, recs: bytes) -> list[tuple[int, np.ndarray]]:
+    """Inverse of ``paper_table_files``: [(r, u_r as uint8 [p~][q~])] in file order."""
+    import struct
+    out = []
+    size = struct.calcsize(PRIMES_RECORD)
+    for k in range(0, len(recs), size):
+        r, off = struct.unpack(PRIMES_RECORD, recs[k:k + size])
+        nb = (r * r + 7) // 8
+        bits = [(blob[off + i // 8] >> (i % 8)) & 1 for i in range(r * r)]
+        out.append((r, np.array(bits, dtype=np.uint8).reshape(r, r)))
+    return out
+
+
+# --------------------------------------------------------------------------------------
+# Theorem 1.1: which roots would give a perfect cuboid
+# --------------------------------------------------------------------------------------
+
+def theorem_1_1_holds(p: int, q: int, t: int) -> bool:
+    """The inequalities of Theorem 1.1 on a positive root t of Q_pq: t > p^2, t > p q,
+    t > q^2 and (p^2 + t)(p q + t) > 2 t^2 (exact integers).  With a coprime p != q
+    such a root is equivalent to a perfect cuboid."""
+    return t > p * p and t > p * q and t > q * q and (p * p + t) * (p * q + t) > 2 * t * t

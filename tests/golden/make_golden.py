@@ -1,7 +1,7 @@
 """Writes the stored expected values of the GPU parity tests.  Calls only the oracle and
 the seeded workload generators (no GPU code).  Run from the repository root:
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py [sieve] [paper_files]
 
 Each output is JSON: {"config", "primes", "order", "ranges": [...], "results": [...]},
 one result per range: n_pairs, counts (caller order), survivors, roots.
@@ -29,7 +29,24 @@ def dump(name, config, primes, ranges, by_density=False):
     print(f"{name}: {time.time() - t0:.1f} s")
 
 
-def main():
+def dump_paper_files(name, primes):
+    """SHA-256 and sizes of the paper's two table files for these primes (section 2)."""
+    import hashlib
+    t0 = time.time()
+    blob, recs = O.paper_table_files(primes)
+    out = {"primes": primes, "bit_tables_bytes": len(blob), "primes_bytes": len(recs),
+           "bit_tables_sha256": hashlib.sha256(blob).hexdigest(),
+           "primes_sha256": hashlib.sha256(recs).hexdigest()}
+    with open(os.path.join(HERE, name), "w") as f:
+        json.dump(out, f, indent=1)
+    print(f"{name}: {time.time() - t0:.1f} s")
+
+
+def main(which):
+    if "paper_files" in which:
+        dump_paper_files("paper_files_11_541.json", W.primes_between(11, 541))
+    if "sieve" not in which:
+        return
     c2 = W.c2()
     dump("c2_as_given.json", c2["name"], c2["primes"], c2["ranges"])
     dump("c2_by_density.json", c2["name"], c2["primes"], c2["ranges"], by_density=True)
@@ -42,4 +59,4 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1:] or ["sieve", "paper_files"])

@@ -434,3 +434,83 @@ def test_deepest_prime():
     assert O.deepest_prime(T, [5, 0, 2, 0], 0) == (3, 17)
     assert O.deepest_prime(T, [0, 0, 0, 0], 0) == (0, 0)
     assert O.deepest_prime(T, [1, 0, 0, 0], 3) == (4, 19)
+
+
+# ---------------------------------------------------------------- table files (section 2)
+
+def test_paper_files_layout():
+    """The bit tables file starts with the printed u_11 bytes of Eq. 2.6; records are
+    8 bytes {short prime; pad; unsigned int offset} and offsets are running sums of
+    ceil(r^2/8); reading the files back gives the tables."""
+    import struct
+    primes = [11, 13, 17, 5]
+    blob, recs = O.paper_table_files(primes)
+    for row in _read_rows("u11_bytes_eq2_6.txt"):          # the bytes printed in Eq. 2.6
+        idx, bits = row.split()
+        assert blob[int(idx)] == int(bits, 2)
+    sizes = [(r * r + 7) // 8 for r in primes]
+    assert len(blob) == sum(sizes) and len(recs) == 8 * len(primes)
+    offs = [0, sizes[0], sizes[0] + sizes[1], sizes[0] + sizes[1] + sizes[2]]
+    for k, r in enumerate(primes):
+        rec = recs[8 * k:8 * k + 8]
+        assert rec[2:4] == b"\0\0"
+        assert struct.unpack("<h", rec[:2])[0] == r and struct.unpack("<I", rec[4:])[0] == offs[k]
+    back = O.read_paper_table_files(blob, recs)
+    assert [r for r, _ in back] == primes
+    for r, u in back:
+        assert (u == O.unsolvable_table(r)).all()
+
+
+def test_eq_2_7_limits():
+    """Eq. 2.7: the tables of the primes from 11 on fit 32-bit offsets up to the prime
+    just below 9697 and no further; 100 primes from 11 (to 569) need under 1.5 MB."""
+    import sympy
+    total, last_ok = 0, None
+    for r in sympy.primerange(11, 20000):
+        total += r * r / 8
+        if total >= 2 ** 32:
+            assert r == 9697 and last_ok < 9697
+            break
+        last_ok = r
+    first100 = list(sympy.primerange(11, 600))[:100]
+    assert first100[-1] == 569
+    assert sum((r * r + 7) // 8 for r in first100) < 1.5 * 2 ** 20
+
+
+# ---------------------------------------------------------------- Theorem 1.1
+
+def test_theorem_1_1_threshold_by_quadratic():
+    """Above max(p^2, pq, q^2), (p^2 + t)(pq + t) > 2 t^2 is t^2 - (p^2 + pq) t - p^3 q < 0,
+    i.e. t below the positive root x* = ((p^2 + pq) + sqrt((p^2 + pq)^2 + 4 p^3 q)) / 2;
+    the largest such integer t is found with an integer square root and the check flips
+    exactly there."""
+    g = random.Random(11)
+    for _ in range(400):
+        p, q = g.randint(1, 10 ** 6), g.randint(1, 10 ** 6)
+        b, c = p * p + p * q, p ** 3 * q
+        disc = b * b + 4 * c
+        def below_root(t):                          # t < x*  <=>  2t - b < sqrt(disc)
+            return 2 * t - b < 0 or (2 * t - b) ** 2 < disc
+        t_star = (b + math.isqrt(disc)) // 2
+        while not below_root(t_star):
+            t_star -= 1
+        while below_root(t_star + 1):
+            t_star += 1
+        lo = max(p * p, p * q, q * q)
+        for t in (t_star - 1, t_star, t_star + 1, t_star + 2, lo, lo + 1):
+            if t <= 0:
+                continue
+            want = t > lo and t <= t_star
+            assert O.theorem_1_1_holds(p, q, t) == want, (p, q, t)
+
+
+def test_theorem_1_1_small_window():
+    """p = 2, q = 1: the window is 5 <= t <= 7 (x* = 3 + sqrt(17) = 7.12)."""
+    assert [t for t in range(1, 20) if O.theorem_1_1_holds(2, 1, t)] == [5, 6, 7]
+
+
+def test_diagonal_roots_are_not_cuboids():
+    """The roots t = k^2 of the pairs p = q sit on the boundary t = p^2 (Theorem 1.1
+    asks for t > p^2), so they never give a cuboid."""
+    for k in (1, 2, 7, 1000, 2 ** 31 + 11):
+        assert not O.theorem_1_1_holds(k, k, k * k)
