@@ -60,6 +60,8 @@ extern "C" {
                                          number of unsolvable k over r + 1; ties: smaller r */
 #define CUBOID_BUILD_REDUCED     0x0u /* u_r from v_r(k)=u_r(k,1) by homogeneity (default) */
 #define CUBOID_BUILD_FULL        0x2u /* u_r by trying every t for every (p~, q~) */
+#define CUBOID_TABLES_IMPORTED   0x10u /* info flag: the tables came from paper-format files */
+#define CUBOID_IMPORT_CHECK      0x8u /* import: compare every table with the definition */
 
 /* ------------------------------------------------------------ range flags */
 #define CUBOID_Q_LT_P            0x1u /* only q < p (q <= p with ALLOW_DIAGONAL) */
@@ -143,6 +145,33 @@ int cuboid_tables_copy_bits(const cuboid_tables* t, uint32_t prime_idx, uint8_t*
  * Synchronous.  Errors: EINVAL, EOVERFLOW (cap < r). */
 int cuboid_tables_copy_reduced(const cuboid_tables* t, uint32_t prime_idx, uint8_t* dst,
                                size_t cap);
+
+/* The paper's two table files (section 2; written by Write_pq_file_stream, section 3,
+ * and loaded by Load_Cuboid_Binaries, section 5):
+ *   bit tables file: for each prime in the caller's order, its r x r table u_r in the
+ *     Eq. 2.6 byte layout (ceil(r^2 / 8) bytes: bit p~ r + q~, least significant bit
+ *     first, last byte zero-padded), tables back to back;
+ *   primes file: one 8-byte little-endian record per prime, the C struct
+ *     {short prime; unsigned int offset;} -- int16 prime, 2 zero padding bytes, uint32
+ *     byte offset of the prime's table in the bit tables file (Eq. 2.7 keeps the offsets
+ *     below 2^32).
+ * Export writes both files (overwriting them) and returns the bit tables' size in
+ * *bytes_written.  Host-synchronous.  Errors: ENOTABLES; EINVAL (NULL path, file not
+ * writable); ERANGE (a prime above 32767 or offsets past 2^32). */
+int cuboid_tables_export(const cuboid_tables* t, const char* bit_tables_path, const char* primes_path,
+                         uint64_t* bytes_written);
+
+/* Build tables from the two files: the file's bits become the device tables as they are
+ * (the reduced table v_r is read from them, v_r(k) = u_r(k, 1)), in the order given by
+ * flags (CUBOID_ORDER_*).  With CUBOID_IMPORT_CHECK every table is also compared with a
+ * table built from the definition, and a difference gives CUBOID_EVERIFY.  *bytes_loaded
+ * receives the primes file's size (the value the paper's loader returns).  cuboid_tables_info
+ * reports CUBOID_TABLES_IMPORTED among the flags.  Synchronous on stream.  Errors: EINVAL
+ * (unreadable file, primes file not a whole number of records, a record's prime not a
+ * prime in [2, 9697), repeated, or a table's padding bits not zero); ERANGE (a table past
+ * the end of the bit tables file); those of cuboid_tables_build; EVERIFY. */
+int cuboid_tables_import(const char* bit_tables_path, const char* primes_path, uint32_t flags, void* stream,
+                         cuboid_tables** out, uint64_t* bytes_loaded);
 
 /* Set / read the kernel shape used by later sieve calls on these tables. */
 int cuboid_tables_set_tuning(cuboid_tables* t, const cuboid_tuning* tune);
@@ -321,6 +350,14 @@ int cuboid_search_stop(cuboid_search* s, cuboid_search_report* rep, uint64_t* co
  * line "Y-M-D HH:MM" and "Stop with p=<p>, q=<q>, r_max=<r_max>".  Host only.
  * Errors: EINVAL (NULL argument, file not writable). */
 int cuboid_search_report_write(const cuboid_search_report* rep, const char* path);
+
+/* ================================================================ Theorem 1.1 */
+
+/* For each root (p, q, t), flags[i] = 1 when t satisfies the inequalities of Theorem 1.1,
+ * t > p^2, t > p q, t > q^2 and (p^2 + t)(p q + t) > 2 t^2 -- for a coprime p != q such a
+ * root is a perfect cuboid -- else 0 (t = 0 gives 0).  Exact in 256-bit integers.  Host
+ * only; roots and flags are host arrays of n entries.  Errors: EINVAL (NULL with n > 0). */
+int cuboid_theorem11_flags(const cuboid_root* roots, uint64_t n, uint8_t* flags);
 
 /* ================================================================ sharding */
 

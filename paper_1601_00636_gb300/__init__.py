@@ -31,6 +31,7 @@ STATUS_NAMES = {0: "OK", 1: "EBUSY", 2: "ERANGE", 3: "EPMAX", 4: "EQLOW", 5: "EQ
 
 ORDER_AS_GIVEN, ORDER_BY_DENSITY, ORDER_BY_RATE = 0x0, 0x1, 0x4
 BUILD_REDUCED, BUILD_FULL = 0x0, 0x2
+TABLES_IMPORTED, IMPORT_CHECK = 0x10, 0x8
 Q_LT_P, ALLOW_DIAGONAL, ROWS_P, ROWS_Q = 0x1, 0x2, 0x4, 0x8
 MODE_PLAIN, MODE_BATCHED, MODE_COUNT_STEPS, MODE_TIME_SIEVE = 0x0, 0x1, 0x100, 0x200
 
@@ -80,6 +81,8 @@ _SIGS = {
     "cuboid_tables_order": (C.c_int, [_P, C.POINTER(_u32)]),
     "cuboid_tables_copy_bits": (C.c_int, [_P, _u32, C.POINTER(C.c_uint8), C.c_size_t, C.POINTER(C.c_size_t)]),
     "cuboid_tables_copy_reduced": (C.c_int, [_P, _u32, C.POINTER(C.c_uint8), C.c_size_t]),
+    "cuboid_tables_export": (C.c_int, [_P, C.c_char_p, C.c_char_p, C.POINTER(_u64)]),
+    "cuboid_tables_import": (C.c_int, [C.c_char_p, C.c_char_p, _u32, _P, C.POINTER(_P), C.POINTER(_u64)]),
     "cuboid_tables_set_tuning": (C.c_int, [_P, C.POINTER(cuboid_tuning)]),
     "cuboid_tables_get_tuning": (C.c_int, [_P, C.POINTER(cuboid_tuning)]),
     "cuboid_tables_free": (C.c_int, [_P]),
@@ -106,6 +109,7 @@ _SIGS = {
     "cuboid_search_current": (C.c_int, [_P, C.POINTER(_u32), C.POINTER(_u32)]),
     "cuboid_search_stop": (C.c_int, [_P, C.POINTER(cuboid_search_report), C.POINTER(_u64)]),
     "cuboid_search_report_write": (C.c_int, [C.POINTER(cuboid_search_report), C.c_char_p]),
+    "cuboid_theorem11_flags": (C.c_int, [C.POINTER(cuboid_root), _u64, C.POINTER(C.c_uint8)]),
     "cuboid_shard_range": (C.c_int, [C.POINTER(cuboid_range), _u32, _u32, C.POINTER(cuboid_range),
                                      C.POINTER(_u64)]),
     "cuboid_verify_pairs": (C.c_int, [C.POINTER(_u32), C.POINTER(_u32), _u32, _P, C.POINTER(cuboid_root),
@@ -193,6 +197,30 @@ def cuboid_tables_copy_reduced(t, prime_idx: int, r: int) -> bytes:
     return bytes(buf)
 
 
+def cuboid_tables_export(t, bit_tables_path: str, primes_path: str) -> int:
+    """Write the paper's two table files; returns the bit tables file's size in bytes."""
+    n = _u64()
+    _check(_lib.cuboid_tables_export(t, bit_tables_path.encode(), primes_path.encode(), C.byref(n)),
+           "cuboid_tables_export")
+    return n.value
+
+
+def cuboid_tables_import(bit_tables_path: str, primes_path: str, flags: int = 0, stream=None):
+    """Tables from the paper's two files; returns (handle, bytes of the primes file)."""
+    out, n = _P(), _u64()
+    _check(_lib.cuboid_tables_import(bit_tables_path.encode(), primes_path.encode(), flags, _stream(stream),
+                                     C.byref(out), C.byref(n)), "cuboid_tables_import")
+    return out.value, n.value
+
+
+def cuboid_tables_import_status(bit_tables_path: str, primes_path: str, flags: int = 0, stream=None):
+    """As cuboid_tables_import, returning (status, handle or None) instead of raising."""
+    out, n = _P(), _u64()
+    st = _lib.cuboid_tables_import(bit_tables_path.encode(), primes_path.encode(), flags, _stream(stream),
+                                   C.byref(out), C.byref(n))
+    return st, (out.value if st == OK else None)
+
+
 def cuboid_tables_set_tuning(t, block_threads=0, ctas_per_sm=0, smem_primes=0, tiles_per_warp=0, hot_primes=0):
     tu = cuboid_tuning(block_threads, ctas_per_sm, smem_primes, tiles_per_warp, hot_primes, 0)
     _check(_lib.cuboid_tables_set_tuning(t, C.byref(tu)), "cuboid_tables_set_tuning")
@@ -275,7 +303,9 @@ def cuboid_result_get(res, range_idx: int, n_primes: int) -> dict:
                                   C.byref(nr), C.byref(rp)), "cuboid_result_get")
     surv = [(int(sp[i]) >> 32, int(sp[i]) & 0xFFFFFFFF) for i in range(ns.value)]
     roots = [(rp[i].p, rp[i].q, (int(rp[i].t_hi) << 64) | int(rp[i].t_lo)) for i in range(nr.value)]
-    return {"n_pairs": npairs.value, "counts": list(counts), "survivors": surv, "roots": roots}
+    cuboids = [rt for rt, f in zip(roots, cuboid_theorem11_flags(roots)) if f] if roots else []
+    return {"n_pairs": npairs.value, "counts": list(counts), "survivors": surv, "roots": roots,
+            "cuboids": cuboids}
 
 
 def cuboid_result_sieve_ms(res):
@@ -368,6 +398,17 @@ def cuboid_search_report_write(rep: dict, path: str) -> None:
     """Append a report (dict from cuboid_search_stop / cuboid_region_scan) to a text file."""
     r = cuboid_search_report(**rep)
     _check(_lib.cuboid_search_report_write(C.byref(r), path.encode()), "cuboid_search_report_write")
+
+
+def cuboid_theorem11_flags(roots) -> list[bool]:
+    """Theorem 1.1 on (p, q, t) roots: True where t would give a perfect cuboid."""
+    n = len(roots)
+    arr = (cuboid_root * max(n, 1))()
+    for i, (p, q, t) in enumerate(roots):
+        arr[i] = cuboid_root(p, q, t & ((1 << 64) - 1), t >> 64)
+    out = (C.c_uint8 * max(n, 1))()
+    _check(_lib.cuboid_theorem11_flags(arr, n, out), "cuboid_theorem11_flags")
+    return [bool(out[i]) for i in range(n)]
 
 
 def cuboid_shard_range(rng, k: int, i: int):

@@ -144,8 +144,10 @@ struct LaunchShape {
 void fill_hot(SieveArgs& a, const cuboid_tables* t, const LaunchShape& L);
 LaunchShape launch_shape(const cuboid_tables* t);
 
-int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_t s,
-                 cuboid_tables** out);
+// packed: NULL (tables from the definition), or per caller index the host address of the
+// prime's Eq. 2.6 bytes (ceil(r^2 / 8)), which become the full tables as they are.
+int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_t s, cuboid_tables** out,
+                 const uint8_t* const* packed);
 
 int status_from_cuda(cudaError_t e);
 

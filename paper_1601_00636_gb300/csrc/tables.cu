@@ -89,6 +89,22 @@ __global__ void k_reduced(const uint32_t* primes, const unsigned long long* voff
   if (cnt) atomicAdd(&unsolvable[i], cnt);
 }
 
+// v_r(k) = u_r(k, 1) read from full tables (imported files): bit k r + 1 of prime i.
+__global__ void k_reduced_from_bits(const uint32_t* primes, const unsigned long long* voff,
+                                    const unsigned long long* foff, const uint32_t* fbits, uint8_t* vbytes,
+                                    uint32_t* unsolvable) {
+  const uint32_t i = blockIdx.x;
+  const uint32_t r = primes[i];
+  uint32_t cnt = 0;
+  for (uint32_t k = threadIdx.x; k < r; k += blockDim.x) {
+    const uint64_t b = (uint64_t)k * r + 1 % r;
+    const uint8_t u = (uint8_t)((fbits[foff[i] + b / 32] >> (b % 32)) & 1u);
+    vbytes[voff[i] + k] = u;
+    cnt += u;
+  }
+  if (cnt) atomicAdd(&unsolvable[i], cnt);
+}
+
 // Brute-force full tables, bit (a r + b) of prime i at fbits + foff[i] (words).
 __global__ void k_full(const uint32_t* primes, const unsigned long long* foff, uint32_t* fbits) {
   const uint32_t i = blockIdx.y;
@@ -205,8 +221,8 @@ int status_from_cuda(cudaError_t e) {
   return CUBOID_ECUDA;
 }
 
-int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_t s,
-                 cuboid_tables** out) {
+int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_t s, cuboid_tables** out,
+                 const uint8_t* const* packed) {
   if (!primes || !out || n == 0 || n > kMaxPrimes) return CUBOID_EINVAL;
   if (flags & ~(CUBOID_ORDER_BY_DENSITY | CUBOID_ORDER_BY_RATE | CUBOID_BUILD_FULL)) return CUBOID_EINVAL;
   if ((flags & CUBOID_ORDER_BY_DENSITY) && (flags & CUBOID_ORDER_BY_RATE)) return CUBOID_EINVAL;
@@ -222,7 +238,7 @@ int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_
   cuboid_tables* t = new (std::nothrow) cuboid_tables();
   if (!t) return CUBOID_ENOMEM;
   t->n = n;
-  t->flags = flags;
+  t->flags = flags | (packed ? CUBOID_TABLES_IMPORTED : 0u);
   t->primes = pr;
   cudaGetDevice(&t->device);
   cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device);
@@ -237,7 +253,13 @@ int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_
   uint32_t* d_fbits = nullptr;
   int st = CUBOID_OK;
   cudaError_t e = cudaSuccess;
-  const bool full = flags & CUBOID_BUILD_FULL;
+  const bool full = (flags & CUBOID_BUILD_FULL) || packed;
+  std::vector<unsigned long long> foff(n);
+  uint64_t ftot = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    foff[i] = ftot;  // words; the Eq. 2.6 bytes of prime i read as little-endian words
+    ftot += ((uint64_t)pr[i] * pr[i] + 31) / 32;
+  }
 
   // reduced-table offsets (caller order)
   t->vbyte_off.resize(n);
@@ -267,7 +289,20 @@ int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_
   CK(cudaMemcpyAsync(d_voff, t->vbyte_off.data(), n * sizeof(unsigned long long),
                      cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(d_cnt, 0, n * sizeof(uint32_t), s));
-  k_reduced<<<n, 256, 0, s>>>(d_primes, d_voff, t->d_vbytes, d_cnt);
+  if (full) {
+    CK(cudaMalloc(&d_foff, n * sizeof(unsigned long long)));
+    CK(cudaMalloc(&d_fbits, ftot * sizeof(uint32_t)));
+    CK(cudaMemcpyAsync(d_foff, foff.data(), n * sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(d_fbits, 0, ftot * sizeof(uint32_t), s));
+  }
+  if (packed) {
+    for (uint32_t i = 0; i < n; ++i)
+      CK(cudaMemcpyAsync(d_fbits + foff[i], packed[i], ((uint64_t)pr[i] * pr[i] + 7) / 8, cudaMemcpyHostToDevice,
+                         s));
+    k_reduced_from_bits<<<n, 256, 0, s>>>(d_primes, d_voff, d_foff, d_fbits, t->d_vbytes, d_cnt);
+  } else {
+    k_reduced<<<n, 256, 0, s>>>(d_primes, d_voff, t->d_vbytes, d_cnt);
+  }
   CK(cudaGetLastError());
   k_order<<<1, 1024, 0, s>>>(d_primes, d_cnt, n,
                              (flags & CUBOID_ORDER_BY_RATE) ? 2 : ((flags & CUBOID_ORDER_BY_DENSITY) ? 1 : 0), d_order);
@@ -298,17 +333,7 @@ int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_
       goto fail;
     }
   }
-  if (full) {
-    std::vector<unsigned long long> foff(n);
-    uint64_t ftot = 0;
-    for (uint32_t i = 0; i < n; ++i) {
-      foff[i] = ftot;
-      ftot += ((uint64_t)pr[i] * pr[i] + 31) / 32;
-    }
-    CK(cudaMalloc(&d_foff, n * sizeof(unsigned long long)));
-    CK(cudaMalloc(&d_fbits, ftot * sizeof(uint32_t)));
-    CK(cudaMemcpyAsync(d_foff, foff.data(), n * sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(d_fbits, 0, ftot * sizeof(uint32_t), s));
+  if (full && !packed) {
     dim3 grid(std::min<uint32_t>(rmax, 1024), n);
     k_full<<<grid, 256, 0, s>>>(d_primes, d_foff, d_fbits);
     CK(cudaGetLastError());
@@ -372,7 +397,7 @@ using namespace cuboid;
 
 extern "C" int cuboid_tables_build(const uint32_t* primes, uint32_t n, uint32_t flags, void* stream,
                                    cuboid_tables** out) {
-  return build_tables(primes, n, flags, (cudaStream_t)stream, out);
+  return build_tables(primes, n, flags, (cudaStream_t)stream, out, nullptr);
 }
 
 extern "C" int cuboid_tables_info(const cuboid_tables* t, uint32_t* n_primes, uint64_t* device_bytes,

@@ -183,3 +183,27 @@ def test_section6_region_to_154000(cb, stream):
         assert c2 == want["counts"] and rep2["pairs"] == want["pairs"]
     finally:
         cb.cuboid_tables_free(t)
+
+
+def test_theorem11_on_found_roots(cb, stream):
+    """Roots the device finds (the diagonal pairs p = q, t = p^2, sieved with the diagonal
+    allowed) are flagged by Theorem 1.1 exactly as the oracle flags them: none is a cuboid."""
+    primes = W.first_odd_primes(6)
+    T = O.Tables(primes)
+    rng = {"p_lo": 1, "p_hi": 300, "q_lo": 1, "q_hi": 300, "q_lt_p": True, "allow_diagonal": True}
+    want = O.run(primes, [rng], tables=T)["ranges"][0]
+    assert want["roots"]
+    t = _tables(cb, primes, cb.ORDER_AS_GIVEN)
+    try:
+        res = cb.cuboid_sieve(t, 1, 300, 1, 300, cb.Q_LT_P | cb.ALLOW_DIAGONAL, stream)
+        try:
+            cb.cuboid_result_wait(res)
+            got = cb.cuboid_result_get(res, 0, len(primes))
+        finally:
+            cb.cuboid_result_free(res)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert sorted(got["roots"]) == want["roots"]
+    flags = cb.cuboid_theorem11_flags(got["roots"])
+    assert flags == [O.theorem_1_1_holds(*r) for r in got["roots"]] and not any(flags)
+    assert got["cuboids"] == []
