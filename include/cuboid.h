@@ -222,7 +222,9 @@ int cuboid_sieve_into(cuboid_result* res, const cuboid_range* ranges, uint32_t n
 
 /* As cuboid_sieve_into with device-resident ranges (a device pointer to n ranges) and
  * no copy back: results stay on the device until cuboid_result_download.  Invalid
- * ranges are skipped on the device and reported by cuboid_result_wait as ERANGE. */
+ * ranges are skipped on the device and reported by cuboid_result_wait as ERANGE.
+ * CUBOID_MODE_BATCHED copies the ranges in stream order; the plain mode reads them where
+ * they are, so they must stay valid and unchanged until the work on stream completes. */
 int cuboid_sieve_device(cuboid_result* res, const cuboid_range* ranges_dev, uint32_t n,
                         uint32_t mode, void* stream);
 

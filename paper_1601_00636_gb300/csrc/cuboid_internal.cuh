@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "cuboid.h"
@@ -129,11 +130,37 @@ cudaError_t launch_plan(const cuboid_range* ranges, uint32_t first, uint32_t cou
                         unsigned long long* npairs, uint32_t n_primes, uint32_t target_tiles,
                         cudaStream_t s, bool reset);
 cudaError_t launch_reset(DevHeader* hdr, uint32_t n_ranges, cudaStream_t s);
+// pdl: launch as a programmatic dependent of the kernel just before it in the stream (the
+// grid is scheduled while that kernel runs and waits on griddepcontrol.wait before it
+// reads what that kernel wrote).  Only when the previous stream operation is that kernel.
 cudaError_t launch_sieve(const SieveArgs& a, bool count_steps, uint32_t blocks,
-                         uint32_t threads, size_t smem, cudaStream_t s);
+                         uint32_t threads, size_t smem, cudaStream_t s, bool pdl = false);
 size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads);
 cudaError_t sieve_set_smem_limit(bool count_steps, size_t bytes);
-cudaError_t launch_verify(const VerifyArgs& a, uint32_t blocks, cudaStream_t s);
+cudaError_t launch_verify(const VerifyArgs& a, uint32_t blocks, cudaStream_t s, bool pdl = false);
+
+// Programmatic dependent launch: a dependent grid waits here until the grid before it has
+// completed and its writes are visible (a no-op in a grid launched without the attribute);
+// a primary grid lets its dependent be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// cudaLaunchKernelEx with the programmatic-serialization attribute when pdl is set.
+template <class... KArgs, class... Args>
+cudaError_t launch_ex(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                      Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 cudaError_t verify_init_device();   // upload the 62-bit moduli (once per device)
 
 // Sieve launch shape chosen from the tables' tuning (runtime.cu).

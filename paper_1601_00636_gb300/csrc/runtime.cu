@@ -165,20 +165,25 @@ static cudaError_t timing_events(cuboid_result* r, uint32_t launches) {
   return cudaSuccess;
 }
 
+// Captured into a graph: the timing events become event-record nodes (External flag).
+// Without them the sieve and the root test are programmatic dependents of the kernel
+// before them, so each is scheduled while that kernel finishes.
 static cudaError_t enqueue_batched(cuboid_result* r, const LaunchShape& L, bool steps, bool timed,
                                    cudaStream_t s) {
   cudaError_t e = launch_plan(r->d_ranges, 0, 0xFFFFFFFFu, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs,
                               r->t->n, L.target_tiles, s, false);
-  if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[0], s);
-  if (e == cudaSuccess) e = launch_sieve(sieve_args(r, L, 0, 0xFFFFFFFFu), steps, L.blocks, L.threads, L.smem, s);
-  if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[1], s);
-  if (e == cudaSuccess) e = launch_verify(verify_args(r), verify_blocks(r->t), s);
+  if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(r->tev[0], s, cudaEventRecordExternal);
+  if (e == cudaSuccess)
+    e = launch_sieve(sieve_args(r, L, 0, 0xFFFFFFFFu), steps, L.blocks, L.threads, L.smem, s, !timed);
+  if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(r->tev[1], s, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = launch_verify(verify_args(r), verify_blocks(r->t), s, !timed);
   return e;
 }
 
 // Batched: reset + one graph (plan, persistent sieve, root test).  Plain: per range a
 // plan and a sieve launch (the first plan also clears the header), then one root test.
-static cudaError_t run_kernels(cuboid_result* r, uint32_t n, uint32_t mode, cudaStream_t s) {
+static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, uint32_t n, uint32_t mode,
+                               cudaStream_t s) {
   const bool steps = mode & CUBOID_MODE_COUNT_STEPS;
   const bool timed = mode & CUBOID_MODE_TIME_SIEVE;
   const bool batched = (mode & 0xFu) == CUBOID_MODE_BATCHED;
@@ -218,13 +223,13 @@ static cudaError_t run_kernels(cuboid_result* r, uint32_t n, uint32_t mode, cuda
     return cudaGraphLaunch(g, s);
   }
   for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
-    e = launch_plan(r->d_ranges, i, 1, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs, r->t->n, L.target_tiles,
-                    s, i == 0);
+    e = launch_plan(d_ranges, i, 1, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs, r->t->n, L.target_tiles, s,
+                    i == 0);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i], s);
-    if (e == cudaSuccess) e = launch_sieve(sieve_args(r, L, i, 1), steps, L.blocks, L.threads, L.smem, s);
+    if (e == cudaSuccess) e = launch_sieve(sieve_args(r, L, i, 1), steps, L.blocks, L.threads, L.smem, s, !timed);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i + 1], s);
   }
-  if (e == cudaSuccess) e = launch_verify(verify_args(r), verify_blocks(r->t), s);
+  if (e == cudaSuccess) e = launch_verify(verify_args(r), verify_blocks(r->t), s, !timed);
   if (timed) r->timed_launches = n;
   return e;
 }
@@ -334,21 +339,26 @@ int sieve_into(cuboid_result* r, const cuboid_range* ranges, uint32_t n, uint32_
   if ((mode & ~(0xFu | CUBOID_MODE_COUNT_STEPS | CUBOID_MODE_TIME_SIEVE)) || (mode & 0xFu) > CUBOID_MODE_BATCHED)
     return CUBOID_EINVAL;
   if (check_device(r) != CUBOID_OK) return CUBOID_EINVAL;
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
+  const bool batched = (mode & 0xFu) == CUBOID_MODE_BATCHED;
+  const cuboid_range* d_ranges = r->d_ranges;
   if (!device_ranges) {
     const int st = validate_ranges(ranges, n);
     if (st != CUBOID_OK) return st;
     cudaEventSynchronize(r->done);  // the pinned staging may still feed an earlier copy
     std::memcpy(r->h_ranges, ranges, n * sizeof(cuboid_range));
     e = cudaMemcpyAsync(r->d_ranges, r->h_ranges, n * sizeof(cuboid_range), cudaMemcpyHostToDevice, s);
-  } else {
+  } else if (batched) {
+    // the captured graph reads the result's own copy
     e = cudaMemcpyAsync(r->d_ranges, ranges, n * sizeof(cuboid_range), cudaMemcpyDeviceToDevice, s);
+  } else {
+    d_ranges = ranges;  // plain launches read the caller's device ranges in stream order
   }
   if (e != cudaSuccess) return status_from_cuda(e);
   r->n_ranges = n;
   r->downloaded = false;
   r->fetched = false;
-  e = run_kernels(r, n, mode, s);
+  e = run_kernels(r, d_ranges, n, mode, s);
   if (e != cudaSuccess) return status_from_cuda(e);
   if (download) return enqueue_download(r, s);
   e = cudaEventRecord(r->done, s);

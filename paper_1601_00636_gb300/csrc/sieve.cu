@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
   __shared__ unsigned long long s_carry;
   __shared__ unsigned long long s_warp[32];
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  pdl_trigger();  // a dependent sieve grid may start its prologue now
   const uint32_t count = count_arg == kNoRange ? hdr->n_ranges : count_arg;
   __syncthreads();
   if (tid == 0) {
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
   }
   __syncthreads();
   unsigned long long my_words = 0;
+  TilePlan P_first{};  // this thread's first range, kept for the scan below
   for (uint32_t k = tid; k < count; k += blockDim.x) {
     const cuboid_range R = ranges[first + k];
     const uint32_t fl = R.flags;
@@ -97,7 +99,8 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
     }
     P.chunk_words = 1;
     P.tile_end = 0;
-    plan[first + k] = P;
+    if (k == tid) P_first = P;
+    else plan[first + k] = P;
   }
   my_words = warp_sum_u64(my_words);
   if (lane == 0 && my_words) atomicAdd(&s_words, my_words);
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
     unsigned long long tiles = 0;
     TilePlan P;
     if (k < count) {
-      P = plan[first + k];
+      P = base == 0 ? P_first : plan[first + k];
       if (P.x_lo <= P.x_hi) {
         const unsigned long long nw = (P.y_hi >> 6) - (P.y_lo >> 6) + 1;
         const unsigned long long chunk = nw < cw ? nw : cw;
@@ -342,6 +345,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   }
   for (uint32_t i = threadIdx.x; i < a.smem_words; i += blockDim.x) s_tab[i] = __ldg(a.words + i);
   __syncthreads();
+  pdl_wait();     // the plan (header, tile plans, zeroed counts) is complete from here on
+  pdl_trigger();  // the root-test grid may be scheduled as CTAs of this grid retire
 
   uint4* s_fac = s_fac_all + wid * kMaxFactors;
   uint4* s_queue = s_queue_all + wid * kQueue;
@@ -606,23 +611,22 @@ cudaError_t set_attr_all(size_t bytes) {
 }
 
 template <bool S, int M>
-void launch_m(const SieveArgs& a, uint32_t blocks, uint32_t threads, size_t smem, cudaStream_t s) {
+cudaError_t launch_m(const SieveArgs& a, uint32_t blocks, uint32_t threads, size_t smem, cudaStream_t s, bool pdl) {
   switch (a.n_hot) {
-    case 6: k_sieve<S, 6, M><<<blocks, threads, smem, s>>>(a); break;
-    case 5: k_sieve<S, 5, M><<<blocks, threads, smem, s>>>(a); break;
-    case 4: k_sieve<S, 4, M><<<blocks, threads, smem, s>>>(a); break;
-    case 2: k_sieve<S, 2, M><<<blocks, threads, smem, s>>>(a); break;
-    default: k_sieve<S, 0, M><<<blocks, threads, smem, s>>>(a); break;
+    case 6: return launch_ex(k_sieve<S, 6, M>, blocks, threads, smem, s, pdl, a);
+    case 5: return launch_ex(k_sieve<S, 5, M>, blocks, threads, smem, s, pdl, a);
+    case 4: return launch_ex(k_sieve<S, 4, M>, blocks, threads, smem, s, pdl, a);
+    case 2: return launch_ex(k_sieve<S, 2, M>, blocks, threads, smem, s, pdl, a);
+    default: return launch_ex(k_sieve<S, 0, M>, blocks, threads, smem, s, pdl, a);
   }
 }
 
 // The 128-register variant serves shapes with at most 512 threads per SM.
 template <bool S>
-void launch_k(const SieveArgs& a, uint32_t blocks, uint32_t threads, uint32_t per_sm, size_t smem, cudaStream_t s) {
-  if (threads * per_sm <= 512)
-    launch_m<S, 512>(a, blocks, threads, smem, s);
-  else
-    launch_m<S, 1024>(a, blocks, threads, smem, s);
+cudaError_t launch_k(const SieveArgs& a, uint32_t blocks, uint32_t threads, uint32_t per_sm, size_t smem,
+                     cudaStream_t s, bool pdl) {
+  if (threads * per_sm <= 512) return launch_m<S, 512>(a, blocks, threads, smem, s, pdl);
+  return launch_m<S, 1024>(a, blocks, threads, smem, s, pdl);
 }
 
 }  // namespace
@@ -664,13 +668,11 @@ cudaError_t launch_plan(const cuboid_range* ranges, uint32_t first, uint32_t cou
 }
 
 cudaError_t launch_sieve(const SieveArgs& a, bool count_steps, uint32_t blocks, uint32_t threads,
-                         size_t smem, cudaStream_t s) {
+                         size_t smem, cudaStream_t s, bool pdl) {
   const uint32_t per_sm = a.n_sms ? (blocks + a.n_sms - 1) / a.n_sms : 2;
-  if (count_steps)
-    launch_k<true>(a, blocks, threads, per_sm, smem, s);
-  else
-    launch_k<false>(a, blocks, threads, per_sm, smem, s);
-  return cudaGetLastError();
+  const cudaError_t e = count_steps ? launch_k<true>(a, blocks, threads, per_sm, smem, s, pdl)
+                                    : launch_k<false>(a, blocks, threads, per_sm, smem, s, pdl);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace cuboid

@@ -376,6 +376,7 @@ __device__ unsigned __int128 isqrt192(const U192& u) {
 }
 
 __global__ void __launch_bounds__(64) k_verify(VerifyArgs a) {
+  pdl_wait();  // the sieve grid's survivors and header are complete from here on
   ull n = a.hdr->n_surv;
   if (n > a.surv_cap) n = a.surv_cap;
   Ctx C;
@@ -499,9 +500,9 @@ cudaError_t verify_init_device() {
   return e;
 }
 
-cudaError_t launch_verify(const VerifyArgs& a, uint32_t blocks, cudaStream_t s) {
-  k_verify<<<blocks, 64, 0, s>>>(a);
-  return cudaGetLastError();
+cudaError_t launch_verify(const VerifyArgs& a, uint32_t blocks, cudaStream_t s, bool pdl) {
+  const cudaError_t e = launch_ex(k_verify, blocks, 64, 0, s, pdl, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace cuboid

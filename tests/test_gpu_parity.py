@@ -421,6 +421,46 @@ def test_status_codes(cb, stream, c1_tables):
     assert lib.cuboid_result_get(None, 0, None, None, None, None, None, None) == cb.EINVAL
 
 
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_device_resident_ranges_modes(cb, stream, c1_tables, mode):
+    """Plain launches read the caller's device ranges in place, batched ones copy them;
+    both equal the oracle, twice in a row on the same result."""
+    import torch
+    ranges = [W.triangle(200), W.rect(300, 400, 1, 800), W.rect(7, 7, 1, 5000)]
+    arr = cb.ranges_array(ranges)
+    dev = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).cuda()
+    m = cb.MODE_PLAIN if mode == "plain" else cb.MODE_BATCHED
+    want = O.run(W.first_odd_primes(24), ranges)["ranges"]
+    res = cb.cuboid_result_create(c1_tables, 3)
+    try:
+        for _ in range(2):
+            cb.cuboid_sieve_device(res, dev.data_ptr(), 3, m, stream)
+            cb.cuboid_result_download(res, stream)
+            assert cb.cuboid_result_wait(res) == cb.OK
+            _check_against([cb.cuboid_result_get(res, i, 24) for i in range(3)], want)
+    finally:
+        cb.cuboid_result_free(res)
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_sieve_timing_events(cb, stream, c1_tables, mode):
+    """CUBOID_MODE_TIME_SIEVE times the sieve launches in both forms (inside the captured
+    graph through event-record nodes) without changing the results."""
+    rng = [W.triangle(3000), W.rect(100, 900, 1, 4000)]
+    m = (cb.MODE_PLAIN if mode == "plain" else cb.MODE_BATCHED) | cb.MODE_TIME_SIEVE
+    res = cb.cuboid_result_create(c1_tables, 2)
+    try:
+        cb.cuboid_sieve_into(res, rng, m, stream)
+        assert cb.cuboid_result_wait(res) == cb.OK
+        ms, launches = cb.cuboid_result_sieve_ms(res)
+        got = [cb.cuboid_result_get(res, i, 24) for i in range(2)]
+    finally:
+        cb.cuboid_result_free(res)
+    assert launches == (2 if mode == "plain" else 1)
+    assert 0.0 < ms < 1000.0
+    _check_against(got, O.run(W.first_odd_primes(24), rng)["ranges"])
+
+
 def test_device_resident_ranges(cb, stream, c1_tables):
     import torch
     ranges = [W.triangle(200), W.rect(300, 400, 1, 800)]
