@@ -318,7 +318,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   uint4* s_queue_all = s_fac_all + warps * kMaxFactors;                              // [warps][kQueue]
   uint2* s_mtab = reinterpret_cast<uint2*>(s_queue_all + warps * kQueue);            // [kMaskTab]
   uint32_t* s_foff = reinterpret_cast<uint32_t*>(s_mtab + kMaskTab);                 // [64]
-  uint32_t* s_cnt_all = s_foff + 64;                                                  // [warps][n]
+  uint32_t* s_fmag_all = s_foff + 64;                                                 // [warps][kMaxFactors]
+  uint32_t* s_cnt_all = s_fmag_all + warps * kMaxFactors;                             // [warps][n]
   uint32_t* s_tab = s_cnt_all + warps * n;                                            // [smem_words]
 
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) s_info[i] = a.info[i];
@@ -349,6 +350,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   pdl_trigger();  // the root-test grid may be scheduled as CTAs of this grid retire
 
   uint4* s_fac = s_fac_all + wid * kMaxFactors;
+  uint32_t* s_fmag = s_fmag_all + wid * kMaxFactors;
   uint4* s_queue = s_queue_all + wid * kQueue;
   uint32_t* wcnt = s_cnt_all + wid * n;
   const uint32_t count = a.range_count == kNoRange ? a.hdr->n_ranges : a.range_count;
@@ -358,6 +360,25 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   unsigned long long st_words = 0, st_wsteps = 0, st_warpsteps = 0, st_tiles = 0;
   uint32_t qn = 0;       // queued words (warp-uniform), all of range ws.cur_range
   bool q_rows = false;   // orientation of the queued words
+
+  // Per-lane counts of the hot primes and of the pairs sieved, folded into the warp's
+  // counters at each flush: at most kFlushTiles tiles of at most kMaxChunkWords / 32
+  // words a lane, 64 pairs a word, so below 2^24.
+  uint32_t hcnt[K > 0 ? K : 1];
+#pragma unroll
+  for (int h = 0; h < (K > 0 ? K : 1); ++h) hcnt[h] = 0;
+  uint32_t tile_pairs = 0;
+  auto fold = [&]() {
+#pragma unroll
+    for (int h = 0; h < K; ++h) {
+      const uint32_t c = __reduce_add_sync(FULL, hcnt[h]);
+      if (lane == 0 && c) wcnt[h] += c;
+      hcnt[h] = 0;
+    }
+    ws.npairs += __reduce_add_sync(FULL, tile_pairs);
+    tile_pairs = 0;
+    __syncwarp();
+  };
 
   unsigned long long next = 0;
   if (lane == 0) next = atomicAdd(&a.hdr->cursor, 1ull);
@@ -382,6 +403,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     const TilePlan P = count == 1 ? P1 : a.plan[k];
     const unsigned long long tbeg = (k == a.range_first) ? 0ull : a.plan[k - 1].tile_end;
     if (k != ws.cur_range || ws.tiles_since_flush >= kFlushTiles) {
+      fold();
       drain<kSteps>(a, s_info, s_tab, wcnt, s_queue, qn, K, q_rows, ws.cur_range, lane, ws, st_wsteps,
                     st_warpsteps, true);
       flush_counts(ws, wcnt, a, lane);
@@ -436,6 +458,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     const uint32_t dbit_lo = (x & 32) ? 0u : 1u << (x & 31), dbit_hi = (x & 32) ? 1u << (x & 31) : 0u;
 
     // ---- distinct odd prime factors of x (warp-cooperative trial division)
+    // Each lane tests one trial prime per batch; a lane that divides x writes its factor
+    // entry {f, 2048 mod f, mask table base, cap} and its reciprocal, and divides its
+    // prime power out of the cofactor through a warp product.
     uint32_t nfo = 0;
     bool has2 = false;
     {
@@ -450,22 +475,37 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         const uint32_t idx = base + lane;
         const TrialPrime tp = idx < a.n_trial ? a.trial[idx] : TrialPrime{1u, 1u, 0u, 0u};
         const bool hit = idx < a.n_trial && m * tp.inv <= tp.lim;
-        uint32_t bal = __ballot_sync(FULL, hit);
-        while (bal) {
-          const uint32_t b = __ffs(bal) - 1;
-          bal &= bal - 1;
-          const uint32_t f = __shfl_sync(FULL, tp.f, b);
-          const uint32_t inv = __shfl_sync(FULL, tp.inv, b);
-          const uint32_t lim = __shfl_sync(FULL, tp.lim, b);
-          while (m * inv <= lim) m *= inv;  // exact division by f
-          if (lane == 0)
-            s_fac[nfo] = make_uint4(f, kLaneStride % f, f < 64 ? s_foff[f] : kBitTab, f < 64 ? f - 1 : 64u);
-          ++nfo;
+        const uint32_t bal = __ballot_sync(FULL, hit);
+        if (!bal) continue;
+        uint32_t pw = 1u;  // the power of this lane's prime in m
+        if (hit) {
+          uint32_t mm = m * tp.inv;  // m / f, exact
+          pw = tp.f;
+          while (mm * tp.inv <= tp.lim) {
+            mm *= tp.inv;
+            pw *= tp.f;
+          }
+          const uint32_t pos = nfo + __popc(bal & lanemask_lt);
+          const uint32_t f = tp.f;
+          s_fac[pos] = make_uint4(f, mod_min(kLaneStride, f, tp.lim), f < 64 ? s_foff[f] : kBitTab,
+                                  f < 64 ? f - 1 : 64u);
+          s_fmag[pos] = tp.lim;  // floor(2^32 / f) for odd f > 1
         }
+#pragma unroll
+        for (int d = 16; d; d >>= 1) pw *= __shfl_xor_sync(FULL, pw, d);
+        uint32_t inv = pw;  // pw^-1 mod 2^32 (pw odd) by Newton's iteration
+#pragma unroll
+        for (int it = 0; it < 4; ++it) inv *= 2u - pw * inv;
+        m *= inv;  // exact: pw divides m
+        nfo += __popc(bal);
       }
-      if (m > 1) {
-        if (lane == 0)
-          s_fac[nfo] = make_uint4(m, kLaneStride % m, m < 64 ? s_foff[m] : kBitTab, m < 64 ? m - 1 : 64u);
+      if (m > 1) {  // a prime: above every trial prime tested, or below 9 if no batch ran
+        if (lane == 0) {
+          const uint32_t mag = 0xFFFFFFFFu / m;
+          s_fac[nfo] = make_uint4(m, mod_min(kLaneStride, m, mag), m < 64 ? s_foff[m] : kBitTab,
+                                  m < 64 ? m - 1 : 64u);
+          s_fmag[nfo] = mag;
+        }
         ++nfo;
       }
       // inert entries up to kFacRegs: offset 64 that never moves, empty mask
@@ -481,8 +521,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         tf[i] = 64u;  // inert entry
         if ((uint32_t)i < nfo) {
           const uint32_t f = s_fac[i].x;
-          const uint32_t s = y0f % f;
-          tf[i] = s ? f - s : 0u;
+          const uint32_t r = mod_min(y0f, f, s_fmag[i]);
+          tf[i] = r ? f - r : 0u;
         }
       }
     }
@@ -496,10 +536,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
       sh[h] = mod_min((wbeg + lane) << 6, a.hot_r[h], a.hot_magic[h]);
     }
 
-    uint32_t hcnt[K > 0 ? K : 1];
-#pragma unroll
-    for (int h = 0; h < (K > 0 ? K : 1); ++h) hcnt[h] = 0;
-    uint32_t tile_pairs = 0;
 
     for (uint32_t wb = wbeg; wb <= wend; wb += 32) {
       const uint32_t w = wb + lane;
@@ -523,7 +559,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         }
         for (uint32_t i = kFacRegs; i < nfo; ++i) {
           const uint4 fc = s_fac[i];
-          const uint32_t s = y0 % fc.x;
+          const uint32_t s = mod_min(y0, fc.x, s_fmag[i]);
           const uint32_t t = s ? fc.x - s : 0u;
           const uint2 mk = s_mtab[fc.z + min(t, fc.w)];
           al &= ~mk.x;
@@ -565,19 +601,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
                       false);
       }
     }
-    // tile totals
-#pragma unroll
-    for (int h = 0; h < K; ++h) {
-      const uint32_t c = __reduce_add_sync(FULL, hcnt[h]);
-      if (lane == 0 && c) wcnt[h] += c;
-    }
     if constexpr (K > 0) {
       if ((uint32_t)(K - 1) > ws.imax) ws.imax = (uint32_t)(K - 1);
     }
-    ws.npairs += __reduce_add_sync(FULL, tile_pairs);
-    __syncwarp();
     next = __shfl_sync(FULL, next, 0);
   }
+  fold();
   drain<kSteps>(a, s_info, s_tab, wcnt, s_queue, qn, K, q_rows, ws.cur_range, lane, ws, st_wsteps, st_warpsteps,
                 true);
   flush_counts(ws, wcnt, a, lane);
@@ -635,6 +664,7 @@ size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads
   const uint32_t warps = threads / 32;
   return (size_t)n_primes * sizeof(PrimeInfo) + (size_t)warps * kMaxFactors * sizeof(uint4) +
          (size_t)warps * kQueue * sizeof(uint4) + kMaskTab * sizeof(uint2) + 64 * sizeof(uint32_t) +
+         (size_t)warps * kMaxFactors * sizeof(uint32_t) +
          (size_t)warps * n_primes * sizeof(uint32_t) + (size_t)smem_words * sizeof(uint32_t);
 }
 
