@@ -100,7 +100,9 @@ typedef struct cuboid_tuning {
   uint32_t smem_primes;     /* how many leading primes (effective order) sit in shared memory */
   uint32_t tiles_per_warp;  /* target number of work tiles per warp (sets the tile size) */
   uint32_t hot_primes;      /* leading primes tested without an early-exit check (0..8) */
-  uint32_t reserved;        /* must be 0 */
+  uint32_t row_lanes;       /* lanes sieving one row: 8, 16 or 32 (a warp then takes 4, 2 or
+                               1 rows at a time; fewer lanes share a row's setup among fewer
+                               words, which pays on short rows) */
 } cuboid_tuning;
 
 /* Instrumentation filled by runs with CUBOID_MODE_COUNT_STEPS. */
@@ -178,7 +180,7 @@ int cuboid_tables_set_tuning(cuboid_tables* t, const cuboid_tuning* tune);
 int cuboid_tables_get_tuning(const cuboid_tables* t, cuboid_tuning* tune);
 
 /* Autotuner: time kernel shapes (hot primes, tiles per warp, threads per CTA, CTAs per
- * SM, primes in shared memory) by coordinate descent on these very ranges (host array,
+ * SM, primes in shared memory, lanes per row) by coordinate descent on these very ranges (host array,
  * n >= 1, mode CUBOID_MODE_PLAIN or CUBOID_MODE_BATCHED), set the fastest on the tables
  * and return it with its time in milliseconds (either pointer may be NULL).  Every
  * candidate must give the same counts, pair totals and survivor/root totals; otherwise

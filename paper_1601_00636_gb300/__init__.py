@@ -60,7 +60,7 @@ class cuboid_root(C.Structure):
 class cuboid_tuning(C.Structure):
     _fields_ = [("block_threads", C.c_uint32), ("ctas_per_sm", C.c_uint32),
                 ("smem_primes", C.c_uint32), ("tiles_per_warp", C.c_uint32),
-                ("hot_primes", C.c_uint32), ("reserved", C.c_uint32)]
+                ("hot_primes", C.c_uint32), ("row_lanes", C.c_uint32)]
 
 
 class cuboid_stats(C.Structure):
@@ -221,8 +221,9 @@ def cuboid_tables_import_status(bit_tables_path: str, primes_path: str, flags: i
     return st, (out.value if st == OK else None)
 
 
-def cuboid_tables_set_tuning(t, block_threads=0, ctas_per_sm=0, smem_primes=0, tiles_per_warp=0, hot_primes=0):
-    tu = cuboid_tuning(block_threads, ctas_per_sm, smem_primes, tiles_per_warp, hot_primes, 0)
+def cuboid_tables_set_tuning(t, block_threads=0, ctas_per_sm=0, smem_primes=0, tiles_per_warp=0, hot_primes=0,
+                             row_lanes=0):
+    tu = cuboid_tuning(block_threads, ctas_per_sm, smem_primes, tiles_per_warp, hot_primes, row_lanes)
     _check(_lib.cuboid_tables_set_tuning(t, C.byref(tu)), "cuboid_tables_set_tuning")
 
 

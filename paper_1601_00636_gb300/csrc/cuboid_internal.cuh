@@ -109,8 +109,9 @@ struct SieveArgs {
   uint32_t range_count;         // UINT32_MAX: read hdr->n_ranges
   uint32_t n_hot;               // hot primes (0, 2, 4, 5, 6 or 8): the first n_hot of the effective order
   uint32_t hot_r[8], hot_magic[8], hot_off[8], hot_W[8];
-  uint32_t hot_step[8];
-  uint32_t n_sms;               // SMs of the device (picks the register budget of the variant)         // 2048 mod r: a lane's next word starts 32 x 64 values further on
+  uint32_t hot_step[8];          // (64 row_lanes) mod r: a lane's stride between words
+  uint32_t row_lanes;            // lanes per row (8, 16, 32)
+  uint32_t n_sms;               // SMs of the device (picks the register budget of the variant)
 };
 constexpr uint32_t kMaxHot = 8;
 
@@ -128,14 +129,14 @@ struct VerifyArgs {
 cudaError_t launch_plan(const cuboid_range* ranges, uint32_t first, uint32_t count,
                         DevHeader* hdr, TilePlan* plan, unsigned long long* counts,
                         unsigned long long* npairs, uint32_t n_primes, uint32_t target_tiles,
-                        cudaStream_t s, bool reset);
+                        cudaStream_t s, bool reset, uint32_t row_lanes);
 cudaError_t launch_reset(DevHeader* hdr, uint32_t n_ranges, cudaStream_t s);
 // pdl: launch as a programmatic dependent of the kernel just before it in the stream (the
 // grid is scheduled while that kernel runs and waits on griddepcontrol.wait before it
 // reads what that kernel wrote).  Only when the previous stream operation is that kernel.
 cudaError_t launch_sieve(const SieveArgs& a, bool count_steps, uint32_t blocks,
                          uint32_t threads, size_t smem, cudaStream_t s, bool pdl = false);
-size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads);
+size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads, uint32_t row_lanes);
 cudaError_t sieve_set_smem_limit(bool count_steps, size_t bytes);
 cudaError_t launch_verify(const VerifyArgs& a, uint32_t blocks, cudaStream_t s, bool pdl = false);
 
@@ -165,11 +166,12 @@ cudaError_t verify_init_device();   // upload the 62-bit moduli (once per device
 
 // Sieve launch shape chosen from the tables' tuning (runtime.cu).
 struct LaunchShape {
-  uint32_t threads, blocks, n_smem, smem_words, target_tiles, n_hot;
+  uint32_t threads, blocks, n_smem, smem_words, target_tiles, n_hot, row_lanes;
   size_t smem;
 };
 void fill_hot(SieveArgs& a, const cuboid_tables* t, const LaunchShape& L);
-LaunchShape launch_shape(const cuboid_tables* t);
+// count_steps: the step-counting build, which exists for whole-warp rows only.
+LaunchShape launch_shape(const cuboid_tables* t, bool count_steps = false);
 
 // packed: NULL (tables from the definition), or per caller index the host address of the
 // prime's Eq. 2.6 bytes (ceil(r^2 / 8)), which become the full tables as they are.

@@ -86,7 +86,8 @@ extern "C" int cuboid_sieve_noalloc(const cuboid_tables* t, const cuboid_range* 
   e = launch_reset(hdr, n, s);
   if (e == cudaSuccess)
     e = launch_plan(ranges_dev, 0, 0xFFFFFFFFu, hdr, plan, reinterpret_cast<unsigned long long*>(counts_dev),
-                    reinterpret_cast<unsigned long long*>(npairs_dev), t->n, L.target_tiles, s, false);
+                    reinterpret_cast<unsigned long long*>(npairs_dev), t->n, L.target_tiles, s, false,
+                    L.row_lanes);
   if (e == cudaSuccess) {
     SieveArgs a;
     a.info = t->d_info;

@@ -65,13 +65,14 @@ struct cuboid_result {
 
 namespace cuboid {
 
-LaunchShape launch_shape(const cuboid_tables* t) {
+LaunchShape launch_shape(const cuboid_tables* t, bool count_steps) {
   const cuboid_tuning& T = t->tuning;
   LaunchShape L;
   L.threads = T.block_threads ? T.block_threads : kDefaultThreads;
+  L.row_lanes = (count_steps || !T.row_lanes) ? 32u : T.row_lanes;
   const uint32_t ctas = T.ctas_per_sm ? T.ctas_per_sm : kDefaultCtasPerSm;
   const int smem_sm = t->smem_per_sm, smem_blk = t->smem_per_block;
-  const size_t fixed = sieve_smem_bytes(0, t->n, L.threads);
+  const size_t fixed = sieve_smem_bytes(0, t->n, L.threads, L.row_lanes);
   size_t per_cta = std::min<size_t>((size_t)smem_blk, (size_t)smem_sm / ctas - 1024);
   size_t table_budget = per_cta > fixed ? per_cta - fixed : 0;
   if (!T.smem_primes) table_budget = std::min(table_budget, kDefaultTableSmem);
@@ -97,7 +98,7 @@ LaunchShape launch_shape(const cuboid_tables* t) {
       L.n_hot = c;
       break;
     }
-  L.smem = sieve_smem_bytes(L.smem_words, t->n, L.threads);
+  L.smem = sieve_smem_bytes(L.smem_words, t->n, L.threads, L.row_lanes);
   L.blocks = (uint32_t)t->sms * ctas;
   const uint32_t tpw = T.tiles_per_warp ? T.tiles_per_warp : kDefaultTilesPerWarp;
   L.target_tiles = L.blocks * (L.threads / 32) * tpw;
@@ -107,13 +108,14 @@ LaunchShape launch_shape(const cuboid_tables* t) {
 void fill_hot(SieveArgs& a, const cuboid_tables* t, const LaunchShape& L) {
   a.n_hot = L.n_hot;
   a.n_sms = (uint32_t)t->sms;
+  a.row_lanes = L.row_lanes;
   for (uint32_t h = 0; h < kMaxHot; ++h) {
     const PrimeInfo pi = h < L.n_hot ? t->info[h] : PrimeInfo{1u, 0u, 0u, 0u};
     a.hot_r[h] = pi.r;
     a.hot_magic[h] = pi.magic;
     a.hot_off[h] = pi.off;
     a.hot_W[h] = pi.W;
-    a.hot_step[h] = 2048u % pi.r;
+    a.hot_step[h] = (64u * L.row_lanes) % pi.r;
   }
 }
 
@@ -171,7 +173,7 @@ static cudaError_t timing_events(cuboid_result* r, uint32_t launches) {
 static cudaError_t enqueue_batched(cuboid_result* r, const LaunchShape& L, bool steps, bool timed,
                                    cudaStream_t s) {
   cudaError_t e = launch_plan(r->d_ranges, 0, 0xFFFFFFFFu, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs,
-                              r->t->n, L.target_tiles, s, false);
+                              r->t->n, L.target_tiles, s, false, L.row_lanes);
   if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(r->tev[0], s, cudaEventRecordExternal);
   if (e == cudaSuccess)
     e = launch_sieve(sieve_args(r, L, 0, 0xFFFFFFFFu), steps, L.blocks, L.threads, L.smem, s, !timed);
@@ -187,7 +189,7 @@ static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, u
   const bool steps = mode & CUBOID_MODE_COUNT_STEPS;
   const bool timed = mode & CUBOID_MODE_TIME_SIEVE;
   const bool batched = (mode & 0xFu) == CUBOID_MODE_BATCHED;
-  const LaunchShape L = launch_shape(r->t);
+  const LaunchShape L = launch_shape(r->t, steps);
   cudaError_t e = sieve_set_smem_limit(steps, L.smem);
   if (e != cudaSuccess) return e;
   r->timed_launches = 0;
@@ -224,7 +226,7 @@ static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, u
   }
   for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
     e = launch_plan(d_ranges, i, 1, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs, r->t->n, L.target_tiles, s,
-                    i == 0);
+                    i == 0, L.row_lanes);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i], s);
     if (e == cudaSuccess) e = launch_sieve(sieve_args(r, L, i, 1), steps, L.blocks, L.threads, L.smem, s, !timed);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i + 1], s);

@@ -31,7 +31,6 @@ constexpr uint32_t kFlushTiles = 256;       // per-warp uint32 counters are flus
 constexpr uint32_t kMaxChunkWords = 32768;  // 64-value words per tile: at most 2^21 pairs
 constexpr uint32_t kQueue = 64;             // per-warp queue of words that outlive the hot primes
 constexpr int kFacRegs = 4;                 // odd factors whose per-lane offsets sit in registers
-constexpr uint32_t kLaneStride = 2048;      // a lane's next word starts 32 words x 64 values further on
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
   for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
@@ -53,7 +52,8 @@ __global__ void k_reset(DevHeader* hdr, uint32_t n_ranges) {
 __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint32_t first,
                                                uint32_t count_arg, DevHeader* hdr, TilePlan* plan,
                                                unsigned long long* counts, unsigned long long* npairs,
-                                               uint32_t n_primes, uint32_t target_tiles, uint32_t reset) {
+                                               uint32_t n_primes, uint32_t target_tiles, uint32_t reset,
+                                               uint32_t subtiles_per_tile) {
   __shared__ unsigned long long s_words;
   __shared__ unsigned long long s_carry;
   __shared__ unsigned long long s_warp[32];
@@ -105,7 +105,9 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
   my_words = warp_sum_u64(my_words);
   if (lane == 0 && my_words) atomicAdd(&s_words, my_words);
   __syncthreads();
-  unsigned long long cw = (s_words + target_tiles - 1) / (target_tiles ? target_tiles : 1);
+  // chunk size from the target number of subtiles (a tile is subtiles_per_tile of them)
+  const unsigned long long target_sub = (unsigned long long)(target_tiles ? target_tiles : 1) * subtiles_per_tile;
+  unsigned long long cw = (s_words + target_sub - 1) / target_sub;
   if (cw < 1) cw = 1;
   if (cw > kMaxChunkWords) cw = kMaxChunkWords;
 
@@ -119,7 +121,8 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
         const unsigned long long nw = (P.y_hi >> 6) - (P.y_lo >> 6) + 1;
         const unsigned long long chunk = nw < cw ? nw : cw;
         P.chunk_words = (uint32_t)chunk;
-        tiles = ((unsigned long long)(P.x_hi - P.x_lo) + 1) * ((nw + chunk - 1) / chunk);
+        const unsigned long long subtiles = ((unsigned long long)(P.x_hi - P.x_lo) + 1) * ((nw + chunk - 1) / chunk);
+        tiles = (subtiles + subtiles_per_tile - 1) / subtiles_per_tile;
       }
     }
     // block inclusive scan of tiles
@@ -306,20 +309,31 @@ __device__ __forceinline__ void drain(const SieveArgs& a, const PrimeInfo* s_inf
 // memory).
 // kMaxThreads: 1024 keeps every kernel at <= 64 registers (two 512-thread CTAs per SM);
 // 512 lets a single 512-thread CTA per SM use up to 128 registers.
-template <bool kSteps, int K, int kMaxThreads>
+// G: lanes per row.  A warp takes one tile = 32 / G consecutive subtiles of a range (a
+// subtile is one row and one chunk of its 64-value words); each group of G lanes sieves
+// one subtile, its lanes on words G apart.  G = 32 is one subtile per warp; smaller groups
+// share the per-row setup (factors of the row value, residues of the hot primes) among
+// fewer words, which pays on short rows.
+template <bool kSteps, int K, int kMaxThreads, int G>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
+  static_assert(G == 8 || G == 16 || G == 32, "lanes per row");
+  constexpr uint32_t NG = 32 / G;                 // subtiles per tile (groups per warp)
+  constexpr uint32_t kStride = 64u * G;           // a lane's next word starts G words further on
   extern __shared__ uint4 smem_raw[];
   const uint32_t n = a.n_primes;
   const uint32_t warps = blockDim.x >> 5;
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t lanemask_lt = (1u << lane) - 1u;
+  const uint32_t g = lane / G, gl = lane % G;     // group and lane in the group
+  const uint32_t gshift = g * G;
+  const uint32_t gmask = G == 32 ? FULL : ((1u << G) - 1u) << gshift;
   PrimeInfo* s_info = reinterpret_cast<PrimeInfo*>(smem_raw);                       // [n]
-  uint4* s_fac_all = smem_raw + n;                                                    // [warps][kMaxFactors]
-  uint4* s_queue_all = s_fac_all + warps * kMaxFactors;                              // [warps][kQueue]
+  uint4* s_fac_all = smem_raw + n;                                                    // [warps][32][kMaxFactors/..]
+  uint4* s_queue_all = s_fac_all + warps * NG * kMaxFactors;                         // [warps][kQueue]
   uint2* s_mtab = reinterpret_cast<uint2*>(s_queue_all + warps * kQueue);            // [kMaskTab]
   uint32_t* s_foff = reinterpret_cast<uint32_t*>(s_mtab + kMaskTab);                 // [64]
-  uint32_t* s_fmag_all = s_foff + 64;                                                 // [warps][kMaxFactors]
-  uint32_t* s_cnt_all = s_fmag_all + warps * kMaxFactors;                             // [warps][n]
+  uint32_t* s_fmag_all = s_foff + 64;                                                 // [warps][NG][kMaxFactors]
+  uint32_t* s_cnt_all = s_fmag_all + warps * NG * kMaxFactors;                        // [warps][n]
   uint32_t* s_tab = s_cnt_all + warps * n;                                            // [smem_words]
 
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) s_info[i] = a.info[i];
@@ -349,8 +363,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   pdl_wait();     // the plan (header, tile plans, zeroed counts) is complete from here on
   pdl_trigger();  // the root-test grid may be scheduled as CTAs of this grid retire
 
-  uint4* s_fac = s_fac_all + wid * kMaxFactors;
-  uint32_t* s_fmag = s_fmag_all + wid * kMaxFactors;
+  uint4* s_fac = s_fac_all + (wid * NG + g) * kMaxFactors;        // this group's factors
+  uint32_t* s_fmag = s_fmag_all + (wid * NG + g) * kMaxFactors;
   uint4* s_queue = s_queue_all + wid * kQueue;
   uint32_t* wcnt = s_cnt_all + wid * n;
   const uint32_t count = a.range_count == kNoRange ? a.hdr->n_ranges : a.range_count;
@@ -362,8 +376,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   bool q_rows = false;   // orientation of the queued words
 
   // Per-lane counts of the hot primes and of the pairs sieved, folded into the warp's
-  // counters at each flush: at most kFlushTiles tiles of at most kMaxChunkWords / 32
-  // words a lane, 64 pairs a word, so below 2^24.
+  // counters at each flush: at most kFlushTiles tiles of at most kMaxChunkWords / G + 1
+  // words a lane, 64 pairs a word, so below 2^27.
   uint32_t hcnt[K > 0 ? K : 1];
 #pragma unroll
   for (int h = 0; h < (K > 0 ? K : 1); ++h) hcnt[h] = 0;
@@ -418,18 +432,22 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     const uint32_t wbox_lo = P.y_lo >> 6;
     const uint32_t nw = (P.y_hi >> 6) - wbox_lo + 1;
     const uint32_t chunks = (nw + P.chunk_words - 1) / P.chunk_words;
-    const unsigned long long local = tile - tbeg;
+    const unsigned long long n_rows = (unsigned long long)(P.x_hi - P.x_lo) + 1;
+    // this group's subtile: row and chunk
+    const unsigned long long sub = (tile - tbeg) * NG + g;
     unsigned long long row_idx;
     uint32_t chunk;
     if (chunks == 1) {
-      row_idx = local;
+      row_idx = sub;
       chunk = 0;
     } else {
-      row_idx = local / chunks;
-      chunk = (uint32_t)(local - row_idx * chunks);
+      row_idx = sub / chunks;
+      chunk = (uint32_t)(sub - row_idx * chunks);
     }
+    bool live = row_idx < n_rows;  // the last tile of a range may have idle groups
     // triangles with p rows: longest rows (largest p) first
-    const uint32_t x = (tri && !rows_q) ? P.x_hi - (uint32_t)row_idx : P.x_lo + (uint32_t)row_idx;
+    const uint32_t x = !live ? 1u
+                             : ((tri && !rows_q) ? P.x_hi - (uint32_t)row_idx : P.x_lo + (uint32_t)row_idx);
 
     // y range of this row
     unsigned long long ylo = P.y_lo, yhi = P.y_hi;
@@ -447,7 +465,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     const uint32_t c1 = c0 + P.chunk_words - 1;
     const uint32_t wbeg = c0 > wlo ? c0 : wlo;
     const uint32_t wend = c1 < whi ? c1 : whi;
-    if (ylo > yhi || wbeg > wend) {
+    if (ylo > yhi || wbeg > wend) live = false;
+    if (G == 32) {
+      if (!live) {
+        next = __shfl_sync(FULL, next, 0);
+        continue;
+      }
+    } else if (!__any_sync(FULL, live)) {
       next = __shfl_sync(FULL, next, 0);
       continue;
     }
@@ -457,11 +481,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     const uint32_t dword = x >> 6;
     const uint32_t dbit_lo = (x & 32) ? 0u : 1u << (x & 31), dbit_hi = (x & 32) ? 1u << (x & 31) : 0u;
 
-    // ---- distinct odd prime factors of x (warp-cooperative trial division)
+    // ---- distinct odd prime factors of x (trial division shared by the group's lanes)
     // Each lane tests one trial prime per batch; a lane that divides x writes its factor
-    // entry {f, 2048 mod f, mask table base, cap} and its reciprocal, and divides its
-    // prime power out of the cofactor through a warp product.
-    uint32_t nfo = 0;
+    // entry {f, (64 G) mod f, mask table base, cap} and its reciprocal, and divides its
+    // prime power out of the cofactor through a product over the group.
+    uint32_t nfo = 0;  // uniform in the group
     bool has2 = false;
     {
       uint32_t m = x;
@@ -469,15 +493,28 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         has2 = true;
         m >>= __ffs(m) - 1;
       }
-      for (uint32_t base = 0; base < a.n_trial; base += 32) {
-        const uint32_t f0 = __ldg(&a.trial[base].f);
-        if ((unsigned long long)f0 * f0 > m) break;
-        const uint32_t idx = base + lane;
-        const TrialPrime tp = idx < a.n_trial ? a.trial[idx] : TrialPrime{1u, 1u, 0u, 0u};
-        const bool hit = idx < a.n_trial && m * tp.inv <= tp.lim;
-        const uint32_t bal = __ballot_sync(FULL, hit);
-        if (!bal) continue;
-        uint32_t pw = 1u;  // the power of this lane's prime in m
+      bool act = live;
+      for (uint32_t base = 0;; base += G) {
+        if (act) {
+          if (base >= a.n_trial) {
+            act = false;
+          } else {
+            const uint32_t f0 = __ldg(&a.trial[base].f);
+            if ((unsigned long long)f0 * f0 > m) act = false;
+          }
+        }
+        if (G == 32) {
+          if (!act) break;
+        } else if (!__any_sync(FULL, act)) {
+          break;
+        }
+        const uint32_t idx = base + gl;
+        const TrialPrime tp = (act && idx < a.n_trial) ? a.trial[idx] : TrialPrime{1u, 1u, 0u, 0u};
+        const bool hit = act && idx < a.n_trial && m * tp.inv <= tp.lim;
+        const uint32_t wbal = __ballot_sync(FULL, hit);
+        if (!wbal) continue;
+        const uint32_t bal = wbal & gmask;  // this group's hits
+        uint32_t pw = 1u;                   // the power of this lane's prime in m
         if (hit) {
           uint32_t mm = m * tp.inv;  // m / f, exact
           pw = tp.f;
@@ -487,12 +524,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           }
           const uint32_t pos = nfo + __popc(bal & lanemask_lt);
           const uint32_t f = tp.f;
-          s_fac[pos] = make_uint4(f, mod_min(kLaneStride, f, tp.lim), f < 64 ? s_foff[f] : kBitTab,
+          s_fac[pos] = make_uint4(f, mod_min(kStride, f, tp.lim), f < 64 ? s_foff[f] : kBitTab,
                                   f < 64 ? f - 1 : 64u);
           s_fmag[pos] = tp.lim;  // floor(2^32 / f) for odd f > 1
         }
 #pragma unroll
-        for (int d = 16; d; d >>= 1) pw *= __shfl_xor_sync(FULL, pw, d);
+        for (int d = G / 2; d; d >>= 1) pw *= __shfl_xor_sync(FULL, pw, d);  // within the group
         uint32_t inv = pw;  // pw^-1 mod 2^32 (pw odd) by Newton's iteration
 #pragma unroll
         for (int it = 0; it < 4; ++it) inv *= 2u - pw * inv;
@@ -500,30 +537,28 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         nfo += __popc(bal);
       }
       if (m > 1) {  // a prime: above every trial prime tested, or below 9 if no batch ran
-        if (lane == 0) {
+        if (gl == 0) {
           const uint32_t mag = 0xFFFFFFFFu / m;
-          s_fac[nfo] = make_uint4(m, mod_min(kLaneStride, m, mag), m < 64 ? s_foff[m] : kBitTab,
+          s_fac[nfo] = make_uint4(m, mod_min(kStride, m, mag), m < 64 ? s_foff[m] : kBitTab,
                                   m < 64 ? m - 1 : 64u);
           s_fmag[nfo] = mag;
         }
         ++nfo;
       }
       // inert entries up to kFacRegs: offset 64 that never moves, empty mask
-      if (lane < (uint32_t)kFacRegs && lane >= nfo) s_fac[lane] = make_uint4(1u, 0u, kBitTab, 64u);
+      if (gl < (uint32_t)kFacRegs && gl >= nfo) s_fac[gl] = make_uint4(1u, 0u, kBitTab, 64u);
       __syncwarp();
     }
     // per-lane offset of the first multiple of each odd factor in the lane's first word
+    const uint32_t y0f = (wbeg + gl) << 6;
     uint32_t tf[kFacRegs];
-    {
-      const uint32_t y0f = (wbeg + lane) << 6;
 #pragma unroll
-      for (int i = 0; i < kFacRegs; ++i) {
-        tf[i] = 64u;  // inert entry
-        if ((uint32_t)i < nfo) {
-          const uint32_t f = s_fac[i].x;
-          const uint32_t r = mod_min(y0f, f, s_fmag[i]);
-          tf[i] = r ? f - r : 0u;
-        }
+    for (int i = 0; i < kFacRegs; ++i) {
+      tf[i] = 64u;  // inert entry
+      if ((uint32_t)i < nfo) {
+        const uint32_t f = s_fac[i].x;
+        const uint32_t r = mod_min(y0f, f, s_fmag[i]);
+        tf[i] = r ? f - r : 0u;
       }
     }
 
@@ -533,15 +568,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
 #pragma unroll
     for (int h = 0; h < K; ++h) {
       rb[h] = a.hot_off[h] + mod_min(x, a.hot_r[h], a.hot_magic[h]) * a.hot_W[h];
-      sh[h] = mod_min((wbeg + lane) << 6, a.hot_r[h], a.hot_magic[h]);
+      sh[h] = mod_min(y0f, a.hot_r[h], a.hot_magic[h]);
     }
 
-
-    for (uint32_t wb = wbeg; wb <= wend; wb += 32) {
-      const uint32_t w = wb + lane;
+    const uint32_t nit = live ? (wend - wbeg) / G + 1 : 0u;  // words of this lane's group, per lane
+    const uint32_t maxit = G == 32 ? nit : __reduce_max_sync(FULL, nit);
+    uint32_t wb = wbeg;
+    for (uint32_t j = 0; j < maxit; ++j, wb += G) {
+      const uint32_t w = wb + gl;
       const uint32_t y0 = w << 6;
       uint32_t al = 0, ah = 0;
-      if (w <= wend) {
+      if (j < nit && w <= wend) {
         unsigned long long rm = FULL64;
         if (w == wlo) rm &= lo_mask;
         if (w == whi) rm &= hi_mask;
@@ -550,11 +587,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         ah = has2 ? (rmh & 0xAAAAAAAAu) : rmh;
 #pragma unroll
         for (int i = 0; i < kFacRegs; ++i) {  // inert entries give an empty mask
-          const uint4 fc = s_fac[i];          // {f, 2048 mod f, table base, cap}
+          const uint4 fc = s_fac[i];          // {f, (64 G) mod f, table base, cap}
           const uint2 mk = s_mtab[fc.z + min(tf[i], fc.w)];
           al &= ~mk.x;
           ah &= ~mk.y;
-          // the lane's next word starts 2048 further on: t <- (t - 2048) mod f
+          // the lane's next word starts 64 G further on: t <- (t - 64 G) mod f
           tf[i] = tf[i] >= fc.y ? tf[i] - fc.y : tf[i] - fc.y + fc.x;
         }
         for (uint32_t i = kFacRegs; i < nfo; ++i) {
@@ -581,7 +618,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
       for (int h = 0; h < K; ++h) {
         if (kSteps) st_wsteps += (al | ah) ? 1 : 0;
         const uint32_t s = sh[h];
-        const uint32_t sn = s + a.hot_step[h];  // next word: + 2048 mod r, below 2r
+        const uint32_t sn = s + a.hot_step[h];  // next word: + (64 G) mod r, below 2r
         sh[h] = min(sn, sn - a.hot_r[h]);
         const uint32_t* tp = s_tab + rb[h] + (s >> 5);
         const uint32_t w0 = tp[0], w1 = tp[1], w2 = tp[2];
@@ -621,33 +658,54 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   }
 }
 
-template <bool S, int M>
-cudaError_t set_attr_m(size_t bytes) {
+template <bool S, int M, int G>
+cudaError_t set_attr_g(size_t bytes) {
   const int b = (int)bytes;
-  cudaError_t e = cudaFuncSetAttribute(k_sieve<S, 0, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 2, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 4, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 5, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sieve<S, 6, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaError_t e = cudaFuncSetAttribute(k_sieve<S, 0, M, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sieve<S, 2, M, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sieve<S, 4, M, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sieve<S, 5, M, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sieve<S, 6, M, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   return e;
 }
 
+// The step-counting build exists for whole-warp rows only (the counts do not depend on
+// the lanes per row).
 template <bool S>
 cudaError_t set_attr_all(size_t bytes) {
-  cudaError_t e = set_attr_m<S, 1024>(bytes);
-  if (e == cudaSuccess) e = set_attr_m<S, 512>(bytes);
+  cudaError_t e = set_attr_g<S, 1024, 32>(bytes);
+  if (e == cudaSuccess) e = set_attr_g<S, 512, 32>(bytes);
+  if constexpr (!S) {
+    if (e == cudaSuccess) e = set_attr_g<S, 1024, 16>(bytes);
+    if (e == cudaSuccess) e = set_attr_g<S, 512, 16>(bytes);
+    if (e == cudaSuccess) e = set_attr_g<S, 1024, 8>(bytes);
+    if (e == cudaSuccess) e = set_attr_g<S, 512, 8>(bytes);
+  }
   return e;
+}
+
+template <bool S, int M, int G>
+cudaError_t launch_g(const SieveArgs& a, uint32_t blocks, uint32_t threads, size_t smem, cudaStream_t s, bool pdl) {
+  switch (a.n_hot) {
+    case 6: return launch_ex(k_sieve<S, 6, M, G>, blocks, threads, smem, s, pdl, a);
+    case 5: return launch_ex(k_sieve<S, 5, M, G>, blocks, threads, smem, s, pdl, a);
+    case 4: return launch_ex(k_sieve<S, 4, M, G>, blocks, threads, smem, s, pdl, a);
+    case 2: return launch_ex(k_sieve<S, 2, M, G>, blocks, threads, smem, s, pdl, a);
+    default: return launch_ex(k_sieve<S, 0, M, G>, blocks, threads, smem, s, pdl, a);
+  }
 }
 
 template <bool S, int M>
 cudaError_t launch_m(const SieveArgs& a, uint32_t blocks, uint32_t threads, size_t smem, cudaStream_t s, bool pdl) {
-  switch (a.n_hot) {
-    case 6: return launch_ex(k_sieve<S, 6, M>, blocks, threads, smem, s, pdl, a);
-    case 5: return launch_ex(k_sieve<S, 5, M>, blocks, threads, smem, s, pdl, a);
-    case 4: return launch_ex(k_sieve<S, 4, M>, blocks, threads, smem, s, pdl, a);
-    case 2: return launch_ex(k_sieve<S, 2, M>, blocks, threads, smem, s, pdl, a);
-    default: return launch_ex(k_sieve<S, 0, M>, blocks, threads, smem, s, pdl, a);
+  if constexpr (!S) {
+    if (a.row_lanes == 8) return launch_g<S, M, 8>(a, blocks, threads, smem, s, pdl);
+    if (a.row_lanes == 16) return launch_g<S, M, 16>(a, blocks, threads, smem, s, pdl);
   }
+  return launch_g<S, M, 32>(a, blocks, threads, smem, s, pdl);
 }
 
 // The 128-register variant serves shapes with at most 512 threads per SM.
@@ -660,11 +718,12 @@ cudaError_t launch_k(const SieveArgs& a, uint32_t blocks, uint32_t threads, uint
 
 }  // namespace
 
-size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads) {
+size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads, uint32_t row_lanes) {
   const uint32_t warps = threads / 32;
-  return (size_t)n_primes * sizeof(PrimeInfo) + (size_t)warps * kMaxFactors * sizeof(uint4) +
+  const uint32_t groups = 32 / (row_lanes ? row_lanes : 32);
+  return (size_t)n_primes * sizeof(PrimeInfo) + (size_t)warps * groups * kMaxFactors * sizeof(uint4) +
          (size_t)warps * kQueue * sizeof(uint4) + kMaskTab * sizeof(uint2) + 64 * sizeof(uint32_t) +
-         (size_t)warps * kMaxFactors * sizeof(uint32_t) +
+         (size_t)warps * groups * kMaxFactors * sizeof(uint32_t) +
          (size_t)warps * n_primes * sizeof(uint32_t) + (size_t)smem_words * sizeof(uint32_t);
 }
 
@@ -691,9 +750,10 @@ cudaError_t launch_reset(DevHeader* hdr, uint32_t n_ranges, cudaStream_t s) {
 
 cudaError_t launch_plan(const cuboid_range* ranges, uint32_t first, uint32_t count, DevHeader* hdr,
                         TilePlan* plan, unsigned long long* counts, unsigned long long* npairs,
-                        uint32_t n_primes, uint32_t target_tiles, cudaStream_t s, bool reset) {
+                        uint32_t n_primes, uint32_t target_tiles, cudaStream_t s, bool reset,
+                        uint32_t row_lanes) {
   k_plan<<<1, 1024, 0, s>>>(ranges, first, count, hdr, plan, counts, npairs, n_primes, target_tiles,
-                            reset ? 1u : 0u);
+                            reset ? 1u : 0u, 32u / (row_lanes ? row_lanes : 32u));
   return cudaGetLastError();
 }
 

@@ -453,7 +453,9 @@ extern "C" int cuboid_tables_copy_reduced(const cuboid_tables* t, uint32_t prime
 extern "C" int cuboid_tables_set_tuning(cuboid_tables* t, const cuboid_tuning* tune) {
   if (!t) return CUBOID_ENOTABLES;
   if (!tune) return CUBOID_EINVAL;
-  if (tune->block_threads % 32 || tune->block_threads > 1024 || tune->ctas_per_sm > 32 || tune->reserved ||
+  const uint32_t rl = tune->row_lanes;
+  if (tune->block_threads % 32 || tune->block_threads > 1024 || tune->ctas_per_sm > 32 ||
+      (rl != 0 && rl != 8 && rl != 16 && rl != 32) ||
       tune->hot_primes > kMaxHot)
     return CUBOID_EINVAL;
   t->tuning = *tune;

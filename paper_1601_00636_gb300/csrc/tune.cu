@@ -1,7 +1,7 @@
 // K6: autotuner of the sieve kernel shape.
 //
 // Coordinate descent over the kernel-shape knobs (hot primes, tiles per warp, threads per
-// CTA, CTAs per SM, primes staged in shared memory), timing each candidate on the
+// CTA, CTAs per SM, primes staged in shared memory, lanes per row), timing each candidate on the
 // caller's own ranges with CUDA events.  Every candidate's counts, pair totals and
 // survivor/root totals must equal the first candidate's (the arithmetic never depends
 // on the shape); a mismatch is reported as CUBOID_EVERIFY.  The winner is set on the
@@ -63,8 +63,8 @@ bool cache_lookup(const char* path, const std::string& key, cuboid_tuning* tu, f
     char k[512];
     cuboid_tuning x{};
     float m = 0.f;
-    if (sscanf(line, "%511s %u %u %u %u %u %f", k, &x.block_threads, &x.ctas_per_sm, &x.smem_primes,
-               &x.tiles_per_warp, &x.hot_primes, &m) == 7 &&
+    if (sscanf(line, "%511s %u %u %u %u %u %u %f", k, &x.block_threads, &x.ctas_per_sm, &x.smem_primes,
+               &x.tiles_per_warp, &x.hot_primes, &x.row_lanes, &m) == 8 &&
         key == k) {
       *tu = x;  // the last matching line wins
       *ms = m;
@@ -79,8 +79,8 @@ void cache_store(const char* path, const std::string& key, const cuboid_tuning& 
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %u %u %u %u %u %.6f\n", key.c_str(), tu.block_threads, tu.ctas_per_sm, tu.smem_primes,
-          tu.tiles_per_warp, tu.hot_primes, ms);
+  fprintf(f, "%s %u %u %u %u %u %u %.6f\n", key.c_str(), tu.block_threads, tu.ctas_per_sm, tu.smem_primes,
+          tu.tiles_per_warp, tu.hot_primes, tu.row_lanes, ms);
   fclose(f);
 }
 
@@ -152,7 +152,7 @@ extern "C" int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uin
     return CUBOID_OK;
   };
 
-  cuboid_tuning cur{512, 2, 0, 3, 5, 0};
+  cuboid_tuning cur{512, 2, 0, 3, 5, 32};
   float cur_ms = 0.f;
   st = measure(cur, &cur_ms);
   const uint32_t hots[] = {2, 4, 5, 6};
@@ -160,6 +160,7 @@ extern "C" int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uin
   const uint32_t thr[] = {256, 512};
   const uint32_t ctas[] = {1, 2, 4};
   const uint32_t smemp[] = {0, 8, 16, 32};
+  const uint32_t lanes[] = {8, 16, 32};
   for (int pass = 0; pass < 2 && st == CUBOID_OK && !mismatch; ++pass) {
     auto try_dim = [&](auto setter, const uint32_t* vals, int nv) {
       for (int i = 0; i < nv && st == CUBOID_OK && !mismatch; ++i) {
@@ -180,6 +181,7 @@ extern "C" int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uin
     try_dim([](cuboid_tuning& c, uint32_t v) { c.block_threads = v; }, thr, 2);
     try_dim([](cuboid_tuning& c, uint32_t v) { c.ctas_per_sm = v; }, ctas, 3);
     try_dim([](cuboid_tuning& c, uint32_t v) { c.smem_primes = v; }, smemp, 4);
+    try_dim([](cuboid_tuning& c, uint32_t v) { c.row_lanes = v; }, lanes, 3);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -279,11 +279,36 @@ def test_transposed_rectangles(cb, stream, c1_tables):
         assert sorted((q, p) for p, q in x["survivors"]) == y["survivors"]
 
 
+@pytest.mark.parametrize("lanes,tpw", [(8, 0), (16, 0), (8, 1), (16, 64), (8, 16)])
+def test_lanes_per_row_edge_ranges(cb, stream, lanes, tpw):
+    """Rows shared by 8 or 16 lanes (4 or 2 rows a warp): the edge and ragged ranges, the
+    small batched rectangles and random row orientations equal the oracle, both forms."""
+    primes = W.first_odd_primes(24)
+    t = cb.cuboid_tables_build(primes, cb.ORDER_AS_GIVEN, stream)
+    try:
+        cb.cuboid_tables_set_tuning(t, row_lanes=lanes, tiles_per_warp=tpw)
+        ranges = []
+        for i, r in enumerate(_edge_ranges()):
+            r = dict(r)
+            r["flags"] = (0, cb.ROWS_P, cb.ROWS_Q)[i % 3]
+            ranges.append(r)
+        want = O.run(primes, ranges)["ranges"]
+        for mode in (cb.MODE_BATCHED, cb.MODE_PLAIN):
+            st, got = _run(cb, t, 24, ranges, mode, stream)
+            assert st == cb.OK
+            _check_against(got, want)
+    finally:
+        cb.cuboid_tables_free(t)
+
+
 TUNINGS = [dict(), dict(block_threads=256, ctas_per_sm=1), dict(block_threads=1024, ctas_per_sm=1),
            dict(smem_primes=1), dict(smem_primes=64, ctas_per_sm=1, block_threads=512),
            dict(tiles_per_warp=1), dict(tiles_per_warp=64, ctas_per_sm=4, block_threads=128),
            dict(hot_primes=0), dict(hot_primes=2), dict(hot_primes=6, smem_primes=10),
-           dict(hot_primes=6, smem_primes=3)]
+           dict(hot_primes=6, smem_primes=3), dict(row_lanes=8), dict(row_lanes=16),
+           dict(row_lanes=8, tiles_per_warp=1, block_threads=512, ctas_per_sm=1, hot_primes=5),
+           dict(row_lanes=16, tiles_per_warp=64, ctas_per_sm=4, block_threads=128, hot_primes=0),
+           dict(row_lanes=8, block_threads=1024, ctas_per_sm=1, hot_primes=6)]
 
 
 @pytest.mark.parametrize("tune", TUNINGS)
