@@ -235,7 +235,9 @@ int cuboid_result_download(cuboid_result* res, void* stream);
 
 /* Wait for the last enqueued work of res, fetch survivor and root records and sort
  * them.  Returns CUBOID_OK, or EOVERFLOW (a record buffer was too small: counts and
- * pair totals are still exact), ERANGE (a device-side range was invalid) or EVERIFY. */
+ * pair totals are still exact), ERANGE (a device-side range was invalid), EVERIFY, or
+ * ETIMEOUT (a CTA's bulk staging of the tables into shared memory did not complete within
+ * its bounded wait; the results are then incomplete). */
 int cuboid_result_wait(cuboid_result* res);
 
 /* Results of range range_idx (valid after cuboid_result_wait):
@@ -283,7 +285,8 @@ int cuboid_result_free(cuboid_result* res);
  *   roots_dev, root_range_dev, root_cap: device root records (unsorted) and range indices.
  *   totals_dev:     device, 3 uint64: number of survivors, number of roots (both may exceed
  *                   the capacities), and the device status bits (0 = clean; 1 survivor
- *                   overflow, 2 root overflow, 4 invalid range, 8 root test unsettled).
+ *                   overflow, 2 root overflow, 4 invalid range, 8 root test unsettled,
+ *                   16 a CTA's bulk staging of the tables did not complete in time).
  *   stream:         everything is enqueued on it; the call returns without waiting.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture.  All calls share the one array and it

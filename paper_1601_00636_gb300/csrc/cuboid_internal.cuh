@@ -55,6 +55,7 @@ constexpr unsigned kStatusSurvOverflow = 1u;
 constexpr unsigned kStatusRootOverflow = 2u;
 constexpr unsigned kStatusBadRange = 4u;
 constexpr unsigned kStatusVerifyFail = 8u;
+constexpr unsigned kStatusStageTimeout = 16u;  // a CTA's shared-memory staging did not complete
 
 // Odd trial-division primes below 2^16 with the exact-divisibility constants
 // inv = f^-1 mod 2^32 and lim = floor((2^32 - 1) / f):  f | n  <=>  n * inv <= lim.

@@ -73,7 +73,8 @@ LaunchShape launch_shape(const cuboid_tables* t, bool count_steps) {
   const uint32_t ctas = T.ctas_per_sm ? T.ctas_per_sm : kDefaultCtasPerSm;
   const int smem_sm = t->smem_per_sm, smem_blk = t->smem_per_block;
   const size_t fixed = sieve_smem_bytes(0, t->n, L.threads, L.row_lanes);
-  size_t per_cta = std::min<size_t>((size_t)smem_blk, (size_t)smem_sm / ctas - 1024);
+  // (128 bytes left for the kernel's static shared memory: the staging barrier)
+  size_t per_cta = std::min<size_t>((size_t)smem_blk - 128, (size_t)smem_sm / ctas - 1024);
   size_t table_budget = per_cta > fixed ? per_cta - fixed : 0;
   if (!T.smem_primes) table_budget = std::min(table_budget, kDefaultTableSmem);
   const uint32_t want = T.smem_primes ? std::min(T.smem_primes, t->n) : t->n;
@@ -82,7 +83,7 @@ LaunchShape launch_shape(const cuboid_tables* t, bool count_steps) {
   while (k < want) {
     const PrimeInfo& pi = t->info[k];
     const uint64_t end = (uint64_t)pi.off + (uint64_t)pi.r * pi.W;
-    if (end * 4 > table_budget) break;
+    if (((end * 4 + 15) & ~15ull) > table_budget) break;  // staged in whole 16-byte units
     words = end;
     ++k;
   }
@@ -430,7 +431,8 @@ int result_wait(cuboid_result* r) {
   r->stats.warp_steps = H.stats[2];
   r->stats.tiles = H.stats[3];
   int st = CUBOID_OK;
-  if (H.status & kStatusVerifyFail) st = CUBOID_EVERIFY;
+  if (H.status & kStatusStageTimeout) st = CUBOID_ETIMEOUT;
+  else if (H.status & kStatusVerifyFail) st = CUBOID_EVERIFY;
   else if (H.status & kStatusBadRange) st = CUBOID_ERANGE;
   else if (H.status & (kStatusSurvOverflow | kStatusRootOverflow)) st = CUBOID_EOVERFLOW;
   r->wait_status = st;

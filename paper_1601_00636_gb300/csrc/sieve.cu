@@ -207,6 +207,23 @@ __device__ __forceinline__ void flush_counts(WarpState& ws, uint32_t* wcnt, cons
   __syncwarp();
 }
 
+constexpr uint32_t kStageSpins = 1u << 22;  // mbarrier polls before a staging time-out
+
+// Poll an mbarrier phase at most `spins` times (each poll may suspend the thread for a
+// short, hardware-chosen time); true once the phase has completed.
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity, uint32_t spins) {
+  for (uint32_t it = 0; it < spins; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // n mod r for any 32-bit n, with magic = floor(2^32 / r): n - floor(n*magic/2^32) r is
 // n mod r or n mod r + r, and the unsigned minimum with itself minus r picks the residue.
 __device__ __forceinline__ uint32_t mod_min(uint32_t n, uint32_t r, uint32_t magic) {
@@ -327,16 +344,42 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   const uint32_t g = lane / G, gl = lane % G;     // group and lane in the group
   const uint32_t gshift = g * G;
   const uint32_t gmask = G == 32 ? FULL : ((1u << G) - 1u) << gshift;
-  PrimeInfo* s_info = reinterpret_cast<PrimeInfo*>(smem_raw);                       // [n]
-  uint4* s_fac_all = smem_raw + n;                                                    // [warps][32][kMaxFactors/..]
-  uint4* s_queue_all = s_fac_all + warps * NG * kMaxFactors;                         // [warps][kQueue]
-  uint2* s_mtab = reinterpret_cast<uint2*>(s_queue_all + warps * kQueue);            // [kMaskTab]
-  uint32_t* s_foff = reinterpret_cast<uint32_t*>(s_mtab + kMaskTab);                 // [64]
-  uint32_t* s_fmag_all = s_foff + 64;                                                 // [warps][NG][kMaxFactors]
-  uint32_t* s_cnt_all = s_fmag_all + warps * NG * kMaxFactors;                        // [warps][n]
-  uint32_t* s_tab = s_cnt_all + warps * n;                                            // [smem_words]
+  // Dynamic shared memory: the table prefix and the prime records first (both staged by
+  // one bulk copy each), then the per-warp and per-CTA working arrays.
+  const uint32_t tab_bytes = (a.smem_words * 4u + 15u) & ~15u;  // the table buffer has 16 B of slack
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem_raw);                                 // [smem_words]
+  PrimeInfo* s_info = reinterpret_cast<PrimeInfo*>(smem_raw + tab_bytes / 16);             // [n]
+  uint4* s_fac_all = reinterpret_cast<uint4*>(s_info + n);                                 // [warps][NG][kMaxFactors]
+  uint4* s_queue_all = s_fac_all + warps * NG * kMaxFactors;                               // [warps][kQueue]
+  uint2* s_mtab = reinterpret_cast<uint2*>(s_queue_all + warps * kQueue);                  // [kMaskTab]
+  uint32_t* s_foff = reinterpret_cast<uint32_t*>(s_mtab + kMaskTab);                       // [64]
+  uint32_t* s_fmag_all = s_foff + 64;                                                       // [warps][NG][kMaxFactors]
+  uint32_t* s_cnt_all = s_fmag_all + warps * NG * kMaxFactors;                              // [warps][n]
+  __shared__ __align__(8) unsigned long long s_bar;  // completion of the two bulk copies
 
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) s_info[i] = a.info[i];
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&s_bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1u) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // TMA bulk copies global -> shared (16-byte aligned, sizes multiples of 16); the
+    // tables and prime records were written when the tables were built
+    const uint32_t info_bytes = n * (uint32_t)sizeof(PrimeInfo);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tab_bytes + info_bytes)
+                 : "memory");
+    if (tab_bytes)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(s_tab)),
+                   "l"(a.words), "r"(tab_bytes), "r"(bar)
+                   : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(s_info)),
+                 "l"(a.info), "r"(info_bytes), "r"(bar)
+                 : "memory");
+  }
   for (uint32_t i = threadIdx.x; i < warps * n; i += blockDim.x) s_cnt_all[i] = 0;
   for (uint32_t i = threadIdx.x; i < kMaskTab; i += blockDim.x) {
     unsigned long long m = 0;
@@ -358,8 +401,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     }
     s_foff[threadIdx.x] = off;
   }
-  for (uint32_t i = threadIdx.x; i < a.smem_words; i += blockDim.x) s_tab[i] = __ldg(a.words + i);
-  __syncthreads();
+  // bounded wait for the staging: on time-out the CTA records it and leaves once its
+  // copies have landed (or a second bounded wait ends)
+  const bool staged = mbar_wait_parity(bar, 0u, kStageSpins);
+  if (__syncthreads_or(!staged)) {
+    pdl_wait();
+    if (threadIdx.x == 0) atomicOr(&a.hdr->status, kStatusStageTimeout);
+    mbar_wait_parity(bar, 0u, kStageSpins);
+    return;
+  }
   pdl_wait();     // the plan (header, tile plans, zeroed counts) is complete from here on
   pdl_trigger();  // the root-test grid may be scheduled as CTAs of this grid retire
 
@@ -721,10 +771,11 @@ cudaError_t launch_k(const SieveArgs& a, uint32_t blocks, uint32_t threads, uint
 size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads, uint32_t row_lanes) {
   const uint32_t warps = threads / 32;
   const uint32_t groups = 32 / (row_lanes ? row_lanes : 32);
-  return (size_t)n_primes * sizeof(PrimeInfo) + (size_t)warps * groups * kMaxFactors * sizeof(uint4) +
+  return (((size_t)smem_words * 4 + 15) & ~(size_t)15) + (size_t)n_primes * sizeof(PrimeInfo) +
+         (size_t)warps * groups * kMaxFactors * sizeof(uint4) +
          (size_t)warps * kQueue * sizeof(uint4) + kMaskTab * sizeof(uint2) + 64 * sizeof(uint32_t) +
          (size_t)warps * groups * kMaxFactors * sizeof(uint32_t) +
-         (size_t)warps * n_primes * sizeof(uint32_t) + (size_t)smem_words * sizeof(uint32_t);
+         (size_t)warps * n_primes * sizeof(uint32_t);
 }
 
 // The dynamic shared-memory limit is a per-device function attribute: raise it only when
