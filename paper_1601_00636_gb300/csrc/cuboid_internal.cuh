@@ -16,6 +16,26 @@ namespace cuboid {
 constexpr uint32_t kMaxPrimes = 1024;
 constexpr uint32_t kPrimeLimit = 9697;     // r < 9697: the bound derived below Eq. 2.7
 constexpr uint32_t kMaxFactors = 10;       // distinct primes of a 32-bit integer <= 9
+
+// Coprimality mask image: for each odd prime f < 64 and offset t in [0, f) the 64-bit mask
+// of bits t, t + f, t + 2f, ... (as two uint32 halves), then the single bits 1 << t for t in
+// [0, 64) and an empty mask at index 64 (a factor f >= 64 hits a 64-value word at most
+// once); then, for each n < 64, the index of n's first mask if n is an odd prime, else the
+// single-bit block.  Built once with the tables; staged into each CTA's shared memory.
+constexpr uint32_t odd_prime_sum_below(uint32_t lim) {
+  uint32_t s = 0;
+  for (uint32_t f = 3; f < lim; f += 2) {
+    bool prime = true;
+    for (uint32_t d = 3; d * d <= f; d += 2) prime = prime && (f % d != 0);
+    if (prime) s += f;
+  }
+  return s;
+}
+constexpr uint32_t kBitTab = odd_prime_sum_below(64);  // 499: masks of the odd primes below 64
+constexpr uint32_t kMaskTab = kBitTab + 65;            // 64-bit entries of the mask table
+static_assert(kBitTab == 499, "mask table layout");
+constexpr uint32_t kMaskImageWords = 2 * kMaskTab + 64;  // uint32 words: masks, then 64 offsets
+static_assert((kMaskImageWords * 4) % 16 == 0, "bulk-copy size");
 constexpr uint32_t kRowCacheLanes = 32;    // row offsets of the first 32 primes kept per lane
 
 // Per-prime sieve constants, one entry per prime in the effective order.  16 bytes.
@@ -79,6 +99,7 @@ struct cuboid_tables {
   uint8_t* d_vbytes = nullptr;      // v_r bytes, caller order, at vbyte_off[i]
   std::vector<uint64_t> vbyte_off;
   cuboid::TrialPrime* d_trial = nullptr;
+  uint32_t* d_mimg = nullptr;       // coprimality mask image (kMaskImageWords)
   uint32_t n_trial = 0;
   cuboid_tuning tuning{};
   std::atomic<int> users{0};        // servers and searches holding the tables
@@ -95,6 +116,7 @@ struct SieveArgs {
   const PrimeInfo* info;
   const uint32_t* words;
   const TrialPrime* trial;
+  const uint32_t* mimg;          // coprimality mask image
   const TilePlan* plan;
   DevHeader* hdr;
   unsigned long long* counts;   // [range][prime, effective order]

@@ -93,6 +93,7 @@ extern "C" int cuboid_sieve_noalloc(const cuboid_tables* t, const cuboid_range* 
     a.info = t->d_info;
     a.words = t->d_words;
     a.trial = t->d_trial;
+    a.mimg = t->d_mimg;
     a.plan = plan;
     a.hdr = hdr;
     a.counts = reinterpret_cast<unsigned long long*>(counts_dev);

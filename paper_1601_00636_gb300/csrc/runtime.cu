@@ -126,6 +126,7 @@ static SieveArgs sieve_args(cuboid_result* r, const LaunchShape& L, uint32_t fir
   a.info = t->d_info;
   a.words = t->d_words;
   a.trial = t->d_trial;
+  a.mimg = t->d_mimg;
   a.plan = r->d_plan;
   a.hdr = r->d_hdr;
   a.counts = r->d_counts;

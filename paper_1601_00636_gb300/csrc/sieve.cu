@@ -162,23 +162,9 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
 
 // ------------------------------------------------------------------ sieve kernel
 
-// Coprimality masks come from a small table in shared memory: for each odd prime f < 64
-// and offset t in [0, f) the 64-bit mask of bits t, t + f, t + 2f, ...; then the single
-// bits 1 << t for t in [0, 64) and an empty mask at index 64 (a factor f >= 64 hits a
-// 64-value word at most once).
-__constant__ uint32_t kSmallOddPrimes[17] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61};
-constexpr uint32_t odd_prime_sum_below(uint32_t lim) {
-  uint32_t s = 0;
-  for (uint32_t f = 3; f < lim; f += 2) {
-    bool prime = true;
-    for (uint32_t d = 3; d * d <= f; d += 2) prime = prime && (f % d != 0);
-    if (prime) s += f;
-  }
-  return s;
-}
-constexpr uint32_t kBitTab = odd_prime_sum_below(64);  // 499: masks of the odd primes below 64
-constexpr uint32_t kMaskTab = kBitTab + 65;            // entries of the mask table
-static_assert(kBitTab == 499, "mask table layout");
+// Coprimality masks come from the mask image built with the tables (see
+// cuboid_internal.cuh), staged into shared memory with the table prefix.
+constexpr uint32_t kTrialSmem = 256;  // leading trial primes staged in shared memory
 
 struct WarpState {
   uint32_t cur_range;
@@ -344,12 +330,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   const uint32_t g = lane / G, gl = lane % G;     // group and lane in the group
   const uint32_t gshift = g * G;
   const uint32_t gmask = G == 32 ? FULL : ((1u << G) - 1u) << gshift;
-  // Dynamic shared memory: the table prefix and the prime records first (both staged by
-  // one bulk copy each), then the per-warp and per-CTA working arrays.
+  // Dynamic shared memory: the table prefix, the prime records, the leading trial primes
+  // and the coprimality mask image (each staged by one bulk copy), then the per-warp
+  // working arrays.
   const uint32_t tab_bytes = (a.smem_words * 4u + 15u) & ~15u;  // the table buffer has 16 B of slack
+  const uint32_t n_trial_s = a.n_trial < kTrialSmem ? a.n_trial : kTrialSmem;
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem_raw);                                 // [smem_words]
   PrimeInfo* s_info = reinterpret_cast<PrimeInfo*>(smem_raw + tab_bytes / 16);             // [n]
-  uint4* s_fac_all = reinterpret_cast<uint4*>(s_info + n);                                 // [warps][NG][kMaxFactors]
+  TrialPrime* s_trial = reinterpret_cast<TrialPrime*>(s_info + n);                         // [kTrialSmem]
+  uint4* s_fac_all = reinterpret_cast<uint4*>(s_trial + kTrialSmem);                       // [warps][NG][kMaxFactors]
   uint4* s_queue_all = s_fac_all + warps * NG * kMaxFactors;                               // [warps][kQueue]
   uint2* s_mtab = reinterpret_cast<uint2*>(s_queue_all + warps * kQueue);                  // [kMaskTab]
   uint32_t* s_foff = reinterpret_cast<uint32_t*>(s_mtab + kMaskTab);                       // [64]
@@ -368,7 +357,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     // TMA bulk copies global -> shared (16-byte aligned, sizes multiples of 16); the
     // tables and prime records were written when the tables were built
     const uint32_t info_bytes = n * (uint32_t)sizeof(PrimeInfo);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tab_bytes + info_bytes)
+    const uint32_t trial_bytes = n_trial_s * (uint32_t)sizeof(TrialPrime);
+    const uint32_t mimg_bytes = kMaskImageWords * 4u;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(tab_bytes + info_bytes + trial_bytes + mimg_bytes)
                  : "memory");
     if (tab_bytes)
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -379,28 +371,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
                      (uint32_t)__cvta_generic_to_shared(s_info)),
                  "l"(a.info), "r"(info_bytes), "r"(bar)
                  : "memory");
+    if (trial_bytes)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(s_trial)),
+                   "l"(a.trial), "r"(trial_bytes), "r"(bar)
+                   : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(s_mtab)),
+                 "l"(a.mimg), "r"(mimg_bytes), "r"(bar)
+                 : "memory");
   }
   for (uint32_t i = threadIdx.x; i < warps * n; i += blockDim.x) s_cnt_all[i] = 0;
-  for (uint32_t i = threadIdx.x; i < kMaskTab; i += blockDim.x) {
-    unsigned long long m = 0;
-    if (i >= kBitTab) {
-      if (i - kBitTab < 64) m = 1ull << (i - kBitTab);
-    } else {
-      uint32_t base = 0, j = 0;
-      while (base + kSmallOddPrimes[j] <= i) base += kSmallOddPrimes[j++];
-      const uint32_t f = kSmallOddPrimes[j], t = i - base;
-      for (uint32_t b = t; b < 64; b += f) m |= 1ull << b;
-    }
-    s_mtab[i] = make_uint2((uint32_t)m, (uint32_t)(m >> 32));
-  }
-  if (threadIdx.x < 64) {
-    uint32_t base = 0, off = kBitTab;
-    for (uint32_t j = 0; j < 17; ++j) {
-      if (kSmallOddPrimes[j] == threadIdx.x) off = base;
-      base += kSmallOddPrimes[j];
-    }
-    s_foff[threadIdx.x] = off;
-  }
   // bounded wait for the staging: on time-out the CTA records it and leaves once its
   // copies have landed (or a second bounded wait ends)
   const bool staged = mbar_wait_parity(bar, 0u, kStageSpins);
@@ -549,7 +530,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           if (base >= a.n_trial) {
             act = false;
           } else {
-            const uint32_t f0 = __ldg(&a.trial[base].f);
+            const uint32_t f0 = base < n_trial_s ? s_trial[base].f : __ldg(&a.trial[base].f);
             if ((unsigned long long)f0 * f0 > m) act = false;
           }
         }
@@ -559,7 +540,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           break;
         }
         const uint32_t idx = base + gl;
-        const TrialPrime tp = (act && idx < a.n_trial) ? a.trial[idx] : TrialPrime{1u, 1u, 0u, 0u};
+        const TrialPrime tp = !(act && idx < a.n_trial) ? TrialPrime{1u, 1u, 0u, 0u}
+                              : (idx < n_trial_s ? s_trial[idx] : a.trial[idx]);
         const bool hit = act && idx < a.n_trial && m * tp.inv <= tp.lim;
         const uint32_t wbal = __ballot_sync(FULL, hit);
         if (!wbal) continue;
@@ -772,6 +754,7 @@ size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads
   const uint32_t warps = threads / 32;
   const uint32_t groups = 32 / (row_lanes ? row_lanes : 32);
   return (((size_t)smem_words * 4 + 15) & ~(size_t)15) + (size_t)n_primes * sizeof(PrimeInfo) +
+         (size_t)kTrialSmem * sizeof(TrialPrime) +
          (size_t)warps * groups * kMaxFactors * sizeof(uint4) +
          (size_t)warps * kQueue * sizeof(uint4) + kMaskTab * sizeof(uint2) + 64 * sizeof(uint32_t) +
          (size_t)warps * groups * kMaxFactors * sizeof(uint32_t) +

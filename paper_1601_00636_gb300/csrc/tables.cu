@@ -12,7 +12,9 @@
 // order, and can be exported in the byte layout of Eq. 2.6.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "cuboid_internal.cuh"
 
@@ -362,6 +364,36 @@ int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_
     CK(cudaMalloc(&t->d_trial, tp.size() * sizeof(TrialPrime)));
     CK(cudaMemcpyAsync(t->d_trial, tp.data(), tp.size() * sizeof(TrialPrime), cudaMemcpyHostToDevice, s));
   }
+  {
+    // coprimality mask image (layout in cuboid_internal.cuh)
+    static std::vector<uint32_t> img;  // the same for every table set; filled once
+    static std::mutex img_mu;
+    std::lock_guard<std::mutex> lk(img_mu);
+    if (img.empty()) {
+      img.assign(kMaskImageWords, 0);
+      uint32_t base = 0;
+      for (uint32_t f = 3; f < 64; f += 2) {
+        if (!is_prime_host(f)) continue;
+        for (uint32_t t = 0; t < f; ++t) {
+          unsigned long long m = 0;
+          for (uint32_t b = t; b < 64; b += f) m |= 1ull << b;
+          img[2 * (base + t)] = (uint32_t)m;
+          img[2 * (base + t) + 1] = (uint32_t)(m >> 32);
+        }
+        img[2 * kMaskTab + f] = base;
+        base += f;
+      }
+      for (uint32_t b = 0; b < 64; ++b) {
+        const unsigned long long m = 1ull << b;
+        img[2 * (kBitTab + b)] = (uint32_t)m;
+        img[2 * (kBitTab + b) + 1] = (uint32_t)(m >> 32);
+      }
+      for (uint32_t n2 = 0; n2 < 64; ++n2)
+        if (n2 < 3 || n2 % 2 == 0 || !is_prime_host(n2)) img[2 * kMaskTab + n2] = kBitTab;
+    }
+    CK(cudaMalloc(&t->d_mimg, kMaskImageWords * sizeof(uint32_t)));
+    CK(cudaMemcpyAsync(t->d_mimg, img.data(), kMaskImageWords * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+  }
   CK(cudaStreamSynchronize(s));
   CK(verify_init_device());
 
@@ -386,6 +418,7 @@ fail:
   dfree(t->d_words);
   dfree(t->d_vbytes);
   dfree(t->d_trial);
+  dfree(t->d_mimg);
   delete t;
   return st == CUBOID_OK ? CUBOID_ECUDA : st;
 #undef CK
@@ -408,7 +441,7 @@ extern "C" int cuboid_tables_info(const cuboid_tables* t, uint32_t* n_primes, ui
     uint64_t vt = 0;
     for (uint32_t r : t->primes) vt += r;
     *device_bytes = (t->total_words + 4) * 4 + t->n * sizeof(PrimeInfo) + vt +
-                    (uint64_t)t->n_trial * sizeof(TrialPrime);
+                    (uint64_t)t->n_trial * sizeof(TrialPrime) + kMaskImageWords * sizeof(uint32_t);
   }
   if (flags) *flags = t->flags;
   return CUBOID_OK;
@@ -477,6 +510,7 @@ extern "C" int cuboid_tables_free(cuboid_tables* t) {
   cudaFree(t->d_words);
   cudaFree(t->d_vbytes);
   cudaFree(t->d_trial);
+  cudaFree(t->d_mimg);
   delete t;
   return CUBOID_OK;
 }
