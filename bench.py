@@ -456,11 +456,11 @@ def e2e_leg(cb, torch, primes, rng, args):
         if i >= 2:
             cold.append(time.perf_counter() - t0)
     cold.sort()
-    h2d = 24
-    d2h = 8 * len(primes) + 8 + 64
+    h2d = 24  # the range, passed to the plan kernel as an argument
+    d2h = 128 + 8 + 8 * len(primes)  # one copy: device header (padded), pair total, counts
     return {"value": n_pairs / per, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": per * 1e3, "steps": k,
-            "includes": "host range -> device, plan + sieve + root test, counts/survivors/roots -> host",
+            "includes": "host range -> device (kernel argument), plan + sieve + root test, header/counts -> host in one copy (survivor and root records when present)",
             "cold": {"value": n_pairs / cold[len(cold) // 2], "ms_per_step": 1e3 * cold[len(cold) // 2],
                      "h2d_bytes_per_step": h2d + 4 * len(primes),
                      "includes": "also table build from the host prime list and result allocation/free"}}

@@ -152,7 +152,8 @@ struct VerifyArgs {
 cudaError_t launch_plan(const cuboid_range* ranges, uint32_t first, uint32_t count,
                         DevHeader* hdr, TilePlan* plan, unsigned long long* counts,
                         unsigned long long* npairs, uint32_t n_primes, uint32_t target_tiles,
-                        cudaStream_t s, bool reset, uint32_t row_lanes);
+                        cudaStream_t s, bool reset, uint32_t row_lanes,
+                        const cuboid_range* inline_range = nullptr);  // host range passed by value (count 1)
 cudaError_t launch_reset(DevHeader* hdr, uint32_t n_ranges, cudaStream_t s);
 // pdl: launch as a programmatic dependent of the kernel just before it in the stream (the
 // grid is scheduled while that kernel runs and waits on griddepcontrol.wait before it

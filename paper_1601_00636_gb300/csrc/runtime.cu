@@ -27,7 +27,9 @@ struct cuboid_result {
   int device = 0;
   uint32_t max_ranges = 0;
   uint64_t surv_cap = 0, root_cap = 0;
-  // device
+  // device: header, pair totals and counts share one block (one copy brings them back)
+  unsigned char* d_block = nullptr;
+  unsigned char* h_block = nullptr;  // its pinned host mirror
   DevHeader* d_hdr = nullptr;
   cuboid_range* d_ranges = nullptr;
   TilePlan* d_plan = nullptr;
@@ -64,6 +66,13 @@ struct cuboid_result {
 };
 
 namespace cuboid {
+
+// Result block: the device header (padded to 64 bytes), then max_ranges pair totals, then
+// the counts of as many ranges as a run fills.
+constexpr size_t kHdrBytes = (sizeof(DevHeader) + 63) / 64 * 64;
+static size_t result_block_bytes(uint32_t max_ranges, size_t n_counts) {
+  return kHdrBytes + (size_t)max_ranges * sizeof(unsigned long long) + n_counts * sizeof(unsigned long long);
+}
 
 LaunchShape launch_shape(const cuboid_tables* t, bool count_steps) {
   const cuboid_tuning& T = t->tuning;
@@ -186,8 +195,9 @@ static cudaError_t enqueue_batched(cuboid_result* r, const LaunchShape& L, bool 
 
 // Batched: reset + one graph (plan, persistent sieve, root test).  Plain: per range a
 // plan and a sieve launch (the first plan also clears the header), then one root test.
-static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, uint32_t n, uint32_t mode,
-                               cudaStream_t s) {
+// h_ranges (plain runs from host ranges): each plan launch takes its range by value.
+static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, const cuboid_range* h_ranges,
+                               uint32_t n, uint32_t mode, cudaStream_t s) {
   const bool steps = mode & CUBOID_MODE_COUNT_STEPS;
   const bool timed = mode & CUBOID_MODE_TIME_SIEVE;
   const bool batched = (mode & 0xFu) == CUBOID_MODE_BATCHED;
@@ -228,7 +238,7 @@ static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, u
   }
   for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
     e = launch_plan(d_ranges, i, 1, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs, r->t->n, L.target_tiles, s,
-                    i == 0, L.row_lanes);
+                    i == 0, L.row_lanes, h_ranges ? h_ranges + i : nullptr);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i], s);
     if (e == cudaSuccess) e = launch_sieve(sieve_args(r, L, i, 1), steps, L.blocks, L.threads, L.smem, s, !timed);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i + 1], s);
@@ -263,19 +273,15 @@ static void result_release(cuboid_result* r) {
     for (auto ev : r->tev) cudaEventDestroy(ev);
     if (r->cap_stream) cudaStreamDestroy(r->cap_stream);
     if (r->done) cudaEventDestroy(r->done);
-    cudaFree(r->d_hdr);
+    cudaFree(r->d_block);
     cudaFree(r->d_ranges);
     cudaFree(r->d_plan);
-    cudaFree(r->d_counts);
-    cudaFree(r->d_npairs);
     cudaFree(r->d_surv);
     cudaFree(r->d_surv_range);
     cudaFree(r->d_roots);
     cudaFree(r->d_root_range);
-    cudaFreeHost(r->h_hdr);
+    cudaFreeHost(r->h_block);
     cudaFreeHost(r->h_ranges);
-    cudaFreeHost(r->h_counts);
-    cudaFreeHost(r->h_npairs);
   }
   delete r;
 }
@@ -297,19 +303,24 @@ int result_create(const cuboid_tables* t, uint32_t max_ranges, uint64_t surv_cap
   if (e == cudaSuccess) {                             \
     e = (call);                                       \
   }
-  AL(cudaMalloc(&r->d_hdr, sizeof(DevHeader)));
+  const size_t block = result_block_bytes(max_ranges, nc);
+  AL(cudaMalloc(&r->d_block, block));
+  AL(cudaMallocHost(&r->h_block, block));
+  if (e == cudaSuccess) {
+    r->d_hdr = reinterpret_cast<DevHeader*>(r->d_block);
+    r->d_npairs = reinterpret_cast<unsigned long long*>(r->d_block + kHdrBytes);
+    r->d_counts = r->d_npairs + max_ranges;
+    r->h_hdr = reinterpret_cast<DevHeader*>(r->h_block);
+    r->h_npairs = reinterpret_cast<unsigned long long*>(r->h_block + kHdrBytes);
+    r->h_counts = r->h_npairs + max_ranges;
+  }
   AL(cudaMalloc(&r->d_ranges, max_ranges * sizeof(cuboid_range)));
   AL(cudaMalloc(&r->d_plan, max_ranges * sizeof(TilePlan)));
-  AL(cudaMalloc(&r->d_counts, nc * sizeof(unsigned long long)));
-  AL(cudaMalloc(&r->d_npairs, max_ranges * sizeof(unsigned long long)));
   AL(cudaMalloc(&r->d_surv, r->surv_cap * sizeof(unsigned long long)));
   AL(cudaMalloc(&r->d_surv_range, r->surv_cap * sizeof(uint32_t)));
   AL(cudaMalloc(&r->d_roots, r->root_cap * sizeof(cuboid_root)));
   AL(cudaMalloc(&r->d_root_range, r->root_cap * sizeof(uint32_t)));
-  AL(cudaMallocHost(&r->h_hdr, sizeof(DevHeader)));
   AL(cudaMallocHost(&r->h_ranges, max_ranges * sizeof(cuboid_range)));
-  AL(cudaMallocHost(&r->h_counts, nc * sizeof(unsigned long long)));
-  AL(cudaMallocHost(&r->h_npairs, max_ranges * sizeof(unsigned long long)));
   AL(cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming));
   AL(cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking));
   AL(cudaMemset(r->d_hdr, 0, sizeof(DevHeader)));
@@ -322,14 +333,13 @@ int result_create(const cuboid_tables* t, uint32_t max_ranges, uint64_t surv_cap
   return CUBOID_OK;
 }
 
+// Bytes of the result block that one run fills: header, pair totals, counts of n ranges.
+static size_t used_block_bytes(const cuboid_result* r) {
+  return result_block_bytes(r->max_ranges, (size_t)r->n_ranges * r->t->n);
+}
+
 static int enqueue_download(cuboid_result* r, cudaStream_t s) {
-  const size_t nc = (size_t)r->n_ranges * r->t->n;
-  cudaError_t e = cudaMemcpyAsync(r->h_hdr, r->d_hdr, sizeof(DevHeader), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && nc)
-    e = cudaMemcpyAsync(r->h_counts, r->d_counts, nc * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && r->n_ranges)
-    e = cudaMemcpyAsync(r->h_npairs, r->d_npairs, r->n_ranges * sizeof(unsigned long long),
-                        cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaMemcpyAsync(r->h_block, r->d_block, used_block_bytes(r), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaEventRecord(r->done, s);
   if (e == cudaSuccess) r->downloaded = true;
   return status_from_cuda(e);
@@ -346,7 +356,12 @@ int sieve_into(cuboid_result* r, const cuboid_range* ranges, uint32_t n, uint32_
   cudaError_t e = cudaSuccess;
   const bool batched = (mode & 0xFu) == CUBOID_MODE_BATCHED;
   const cuboid_range* d_ranges = r->d_ranges;
-  if (!device_ranges) {
+  const cuboid_range* h_ranges = nullptr;
+  if (!device_ranges && !batched) {
+    const int st = validate_ranges(ranges, n);
+    if (st != CUBOID_OK) return st;
+    h_ranges = ranges;  // plain launches take each range as a kernel argument: no copy
+  } else if (!device_ranges) {
     const int st = validate_ranges(ranges, n);
     if (st != CUBOID_OK) return st;
     cudaEventSynchronize(r->done);  // the pinned staging may still feed an earlier copy
@@ -362,7 +377,7 @@ int sieve_into(cuboid_result* r, const cuboid_range* ranges, uint32_t n, uint32_
   r->n_ranges = n;
   r->downloaded = false;
   r->fetched = false;
-  e = run_kernels(r, d_ranges, n, mode, s);
+  e = run_kernels(r, d_ranges, h_ranges, n, mode, s);
   if (e != cudaSuccess) return status_from_cuda(e);
   if (download) return enqueue_download(r, s);
   e = cudaEventRecord(r->done, s);
@@ -379,11 +394,7 @@ int result_wait(cuboid_result* r) {
   const uint32_t n = r->n_ranges;
   const size_t nc = (size_t)n * t->n;
   if (!r->downloaded) {
-    e = cudaMemcpy(r->h_hdr, r->d_hdr, sizeof(DevHeader), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && nc)
-      e = cudaMemcpy(r->h_counts, r->d_counts, nc * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && n)
-      e = cudaMemcpy(r->h_npairs, r->d_npairs, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(r->h_block, r->d_block, used_block_bytes(r), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return status_from_cuda(e);
   }
   const DevHeader H = *r->h_hdr;

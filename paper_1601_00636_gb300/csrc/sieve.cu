@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
                                                uint32_t count_arg, DevHeader* hdr, TilePlan* plan,
                                                unsigned long long* counts, unsigned long long* npairs,
                                                uint32_t n_primes, uint32_t target_tiles, uint32_t reset,
-                                               uint32_t subtiles_per_tile) {
+                                               uint32_t subtiles_per_tile, cuboid_range inl, uint32_t use_inl) {
   __shared__ unsigned long long s_words;
   __shared__ unsigned long long s_carry;
   __shared__ unsigned long long s_warp[32];
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
   unsigned long long my_words = 0;
   TilePlan P_first{};  // this thread's first range, kept for the scan below
   for (uint32_t k = tid; k < count; k += blockDim.x) {
-    const cuboid_range R = ranges[first + k];
+    const cuboid_range R = use_inl ? inl : ranges[first + k];  // inl: one range passed by value
     const uint32_t fl = R.flags;
     const bool bad = R.p_lo == 0 || R.q_lo == 0 || R.p_lo > R.p_hi || R.q_lo > R.q_hi ||
                      R.reserved != 0 || (fl & ~0xFu) ||
@@ -785,9 +785,10 @@ cudaError_t launch_reset(DevHeader* hdr, uint32_t n_ranges, cudaStream_t s) {
 cudaError_t launch_plan(const cuboid_range* ranges, uint32_t first, uint32_t count, DevHeader* hdr,
                         TilePlan* plan, unsigned long long* counts, unsigned long long* npairs,
                         uint32_t n_primes, uint32_t target_tiles, cudaStream_t s, bool reset,
-                        uint32_t row_lanes) {
+                        uint32_t row_lanes, const cuboid_range* inline_range) {
+  const cuboid_range inl = inline_range ? *inline_range : cuboid_range{};
   k_plan<<<1, 1024, 0, s>>>(ranges, first, count, hdr, plan, counts, npairs, n_primes, target_tiles,
-                            reset ? 1u : 0u, 32u / (row_lanes ? row_lanes : 32u));
+                            reset ? 1u : 0u, 32u / (row_lanes ? row_lanes : 32u), inl, inline_range ? 1u : 0u);
   return cudaGetLastError();
 }
 
