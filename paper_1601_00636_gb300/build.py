@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build", platform.machine())
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libcuboid.so")
-SOURCES = ["tables.cu", "sieve.cu", "verify.cu", "runtime.cu", "server.cu", "noalloc.cu", "tune.cu", "region.cu", "tablefile.cu", "theorem.cu"]
+SOURCES = ["tables.cu", "plan.cu", "sieve.cu", "verify.cu", "runtime.cu", "server.cu", "noalloc.cu", "tune.cu", "region.cu", "tablefile.cu", "theorem.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -15,6 +15,7 @@ namespace cuboid {
 
 constexpr uint32_t kMaxPrimes = 1024;
 constexpr uint32_t kPrimeLimit = 9697;     // r < 9697: the bound derived below Eq. 2.7
+constexpr uint32_t kMaxChunkWords = 32768;   // 64-value words per subtile: at most 2^21 pairs
 constexpr uint32_t kMaxFactors = 10;       // distinct primes of a 32-bit integer <= 9
 
 // Coprimality mask image: for each odd prime f < 64 and offset t in [0, f) the 64-bit mask
