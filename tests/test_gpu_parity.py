@@ -522,3 +522,24 @@ def test_repeat_is_deterministic(cb, stream, c1_tables):
     a = _run(cb, c1_tables, 24, rng, cb.MODE_BATCHED, stream)
     b = _run(cb, c1_tables, 24, rng, cb.MODE_BATCHED, stream)
     assert a == b
+
+
+def test_deep_primes_near_eq_2_7_bound(cb, stream):
+    """Primes up to the largest the table bound below Eq. 2.7 allows (9689 < 9697): the
+    reduced tables equal the oracle's, and sieving with the large primes first equals
+    the oracle on long rows."""
+    primes = [9689, 9679, 9677, 7919, 4999, 11, 13, 17]
+    t = cb.cuboid_tables_build(primes, cb.ORDER_AS_GIVEN, stream)
+    try:
+        for i, r in enumerate(primes[:3]):
+            assert cb.cuboid_tables_copy_reduced(t, i, r) == bytes(O.reduced_table(r))
+        ranges = [W.rect(100000, 100003, 1, 200000), W.rect(9689 * 7, 9689 * 7, 1, 100000),
+                  W.rect(1, 30000, 9677, 9679)]
+        T = O.Tables(primes, full_limit=0)
+        want = O.run(primes, ranges, tables=T)["ranges"]
+        for mode in (cb.MODE_BATCHED, cb.MODE_PLAIN):
+            st, got = _run(cb, t, len(primes), ranges, mode, stream, surv_cap=1 << 20)
+            assert st == cb.OK
+            _check_against(got, want)
+    finally:
+        cb.cuboid_tables_free(t)
