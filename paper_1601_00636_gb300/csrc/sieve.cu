@@ -282,19 +282,23 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   uint32_t qn = 0;       // queued words (warp-uniform), all of range ws.cur_range
   bool q_rows = false;   // orientation of the queued words
 
-  // Per-lane counts of the hot primes and of the pairs sieved, folded into the warp's
-  // counters at each flush: at most kFlushTiles tiles of at most kMaxChunkWords / G + 1
-  // words a lane, 64 pairs a word, so below 2^27.
-  uint32_t hcnt[K > 0 ? K : 1];
+  // Per-lane sums of the pairs still alive: tile_pairs before the hot primes, hs[h] after
+  // hot prime h.  Hot prime h rejected the difference of the sums before and after it (a
+  // pair leaves the alive set once).  Folded into the warp's counters at each flush: at
+  // most kFlushTiles tiles of at most kMaxChunkWords / G + 1 words a lane, 64 pairs a
+  // word, so below 2^27.
+  uint32_t hs[K > 0 ? K : 1];
 #pragma unroll
-  for (int h = 0; h < (K > 0 ? K : 1); ++h) hcnt[h] = 0;
+  for (int h = 0; h < (K > 0 ? K : 1); ++h) hs[h] = 0;
   uint32_t tile_pairs = 0;
   auto fold = [&]() {
+    uint32_t before = tile_pairs;
 #pragma unroll
     for (int h = 0; h < K; ++h) {
-      const uint32_t c = __reduce_add_sync(FULL, hcnt[h]);
+      const uint32_t c = __reduce_add_sync(FULL, before - hs[h]);
       if (lane == 0 && c) wcnt[h] += c;
-      hcnt[h] = 0;
+      before = hs[h];
+      hs[h] = 0;
     }
     ws.npairs += __reduce_add_sync(FULL, tile_pairs);
     tile_pairs = 0;
@@ -479,6 +483,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
       sh[h] = mod_min(y0f, a.hot_r[h], a.hot_magic[h]);
     }
 
+    const uint32_t emask = has2 ? 0xAAAAAAAAu : FULL;  // x even: y0 is even, so even y sit at even bits
     const uint32_t nit = live ? (wend - wbeg) / G + 1 : 0u;  // words of this lane's group, per lane
     const uint32_t maxit = G == 32 ? nit : __reduce_max_sync(FULL, nit);
     uint32_t wb = wbeg;
@@ -491,14 +496,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         if (w == wlo) rm &= lo_mask;
         if (w == whi) rm &= hi_mask;
         const uint32_t rml = (uint32_t)rm, rmh = (uint32_t)(rm >> 32);
-        al = has2 ? (rml & 0xAAAAAAAAu) : rml;  // y0 is even: even y at even bits
-        ah = has2 ? (rmh & 0xAAAAAAAAu) : rmh;
+        uint32_t ml = 0, mh = 0;  // union of the factor masks
 #pragma unroll
         for (int i = 0; i < kFacRegs; ++i) {  // inert entries give an empty mask
           const uint4 fc = s_fac[i];          // {f, (64 G) mod f, table base, cap}
           const uint2 mk = s_mtab[fc.z + min(tf[i], fc.w)];
-          al &= ~mk.x;
-          ah &= ~mk.y;
+          ml |= mk.x;
+          mh |= mk.y;
           // the lane's next word starts 64 G further on: t <- (t - 64 G) mod f
           tf[i] = tf[i] >= fc.y ? tf[i] - fc.y : tf[i] - fc.y + fc.x;
         }
@@ -507,9 +511,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           const uint32_t s = mod_min(y0, fc.x, s_fmag[i]);
           const uint32_t t = s ? fc.x - s : 0u;
           const uint2 mk = s_mtab[fc.z + min(t, fc.w)];
-          al &= ~mk.x;
-          ah &= ~mk.y;
+          ml |= mk.x;
+          mh |= mk.y;
         }
+        al = rml & emask & ~ml;
+        ah = rmh & emask & ~mh;
         if (w == dword) {
           al &= ~dbit_lo;
           ah &= ~dbit_hi;
@@ -530,10 +536,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         sh[h] = min(sn, sn - a.hot_r[h]);
         const uint32_t* tp = s_tab + rb[h] + (s >> 5);
         const uint32_t w0 = tp[0], w1 = tp[1], w2 = tp[2];
-        const uint32_t rl = __funnelshift_r(w0, w1, s) & al, rh = __funnelshift_r(w1, w2, s) & ah;
-        hcnt[h] += __popc(rl) + __popc(rh);
-        al ^= rl;
-        ah ^= rh;
+        al &= ~__funnelshift_r(w0, w1, s);  // the window of u_r(x mod r, y0 mod r ...)
+        ah &= ~__funnelshift_r(w1, w2, s);
+        hs[h] += __popc(al) + __popc(ah);
       }
       if (kSteps) st_warpsteps += K;
       // queue the words still alive
