@@ -74,6 +74,10 @@ extern "C" {
 #define CUBOID_MODE_BATCHED      0x1u /* all ranges in one persistent launch (CUDA graph) */
 #define CUBOID_MODE_COUNT_STEPS  0x100u /* also count sieve steps (cuboid_result_stats) */
 #define CUBOID_MODE_TIME_SIEVE   0x200u /* time the sieve kernel(s) with CUDA events */
+#define CUBOID_MODE_STAGE_TIMEOUT 0x400u /* failure test: every CTA's bounded wait for its
+                                            shared-memory staging gives up at once; the
+                                            CTAs leave once their copies land and the run
+                                            reports CUBOID_ETIMEOUT (plain mode only) */
 
 typedef struct cuboid_tables cuboid_tables;
 typedef struct cuboid_result cuboid_result;

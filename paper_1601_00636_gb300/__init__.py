@@ -34,6 +34,7 @@ BUILD_REDUCED, BUILD_FULL = 0x0, 0x2
 TABLES_IMPORTED, IMPORT_CHECK = 0x10, 0x8
 Q_LT_P, ALLOW_DIAGONAL, ROWS_P, ROWS_Q = 0x1, 0x2, 0x4, 0x8
 MODE_PLAIN, MODE_BATCHED, MODE_COUNT_STEPS, MODE_TIME_SIEVE = 0x0, 0x1, 0x100, 0x200
+MODE_STAGE_TIMEOUT = 0x400
 
 
 class CuboidError(RuntimeError):
@@ -288,9 +289,9 @@ def cuboid_result_download(res, stream=None) -> None:
 
 
 def cuboid_result_wait(res) -> int:
-    """Returns OK, EOVERFLOW, ERANGE or EVERIFY; raises on other errors."""
+    """Returns OK, EOVERFLOW, ERANGE, EVERIFY or ETIMEOUT; raises on other errors."""
     st = _lib.cuboid_result_wait(res)
-    if st not in (OK, EOVERFLOW, ERANGE, EVERIFY):
+    if st not in (OK, EOVERFLOW, ERANGE, EVERIFY, ETIMEOUT):
         _check(st, "cuboid_result_wait")
     return st
 

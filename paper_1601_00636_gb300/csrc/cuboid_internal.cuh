@@ -15,6 +15,7 @@ namespace cuboid {
 
 constexpr uint32_t kMaxPrimes = 1024;
 constexpr uint32_t kPrimeLimit = 9697;     // r < 9697: the bound derived below Eq. 2.7
+constexpr uint32_t kStageSpins = 1u << 22;    // polls of a CTA's staging barrier before it gives up
 constexpr uint32_t kMaxChunkWords = 32768;   // 64-value words per subtile: at most 2^21 pairs
 constexpr uint32_t kMaxFactors = 10;       // distinct primes of a 32-bit integer <= 9
 
@@ -135,6 +136,7 @@ struct SieveArgs {
   uint32_t hot_r[8], hot_magic[8], hot_off[8], hot_W[8];
   uint32_t hot_step[8];          // (64 row_lanes) mod r: a lane's stride between words
   uint32_t row_lanes;            // lanes per row (8, 16, 32)
+  uint32_t stage_spins;          // polls of the staging barrier before a time-out
   uint32_t n_sms;               // SMs of the device (picks the register budget of the variant)
 };
 constexpr uint32_t kMaxHot = 8;

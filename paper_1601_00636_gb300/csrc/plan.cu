@@ -151,7 +151,9 @@ cudaError_t launch_plan(const cuboid_range* ranges, uint32_t first, uint32_t cou
                         uint32_t n_primes, uint32_t target_tiles, cudaStream_t s, bool reset,
                         uint32_t row_lanes, const cuboid_range* inline_range) {
   const cuboid_range inl = inline_range ? *inline_range : cuboid_range{};
-  k_plan<<<1, 1024, 0, s>>>(ranges, first, count, hdr, plan, counts, npairs, n_primes, target_tiles,
+  // one warp plans up to 32 ranges (a plain launch plans one): no block-wide barriers
+  const uint32_t threads = count <= 32 ? 32u : 1024u;
+  k_plan<<<1, threads, 0, s>>>(ranges, first, count, hdr, plan, counts, npairs, n_primes, target_tiles,
                             reset ? 1u : 0u, 32u / (row_lanes ? row_lanes : 32u), inl, inline_range ? 1u : 0u);
   return cudaGetLastError();
 }

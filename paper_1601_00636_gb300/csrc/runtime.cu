@@ -119,6 +119,7 @@ void fill_hot(SieveArgs& a, const cuboid_tables* t, const LaunchShape& L) {
   a.n_hot = L.n_hot;
   a.n_sms = (uint32_t)t->sms;
   a.row_lanes = L.row_lanes;
+  a.stage_spins = kStageSpins;
   for (uint32_t h = 0; h < kMaxHot; ++h) {
     const PrimeInfo pi = h < L.n_hot ? t->info[h] : PrimeInfo{1u, 0u, 0u, 0u};
     a.hot_r[h] = pi.r;
@@ -200,6 +201,7 @@ static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, c
                                uint32_t n, uint32_t mode, cudaStream_t s) {
   const bool steps = mode & CUBOID_MODE_COUNT_STEPS;
   const bool timed = mode & CUBOID_MODE_TIME_SIEVE;
+  const bool stage_fail = mode & CUBOID_MODE_STAGE_TIMEOUT;
   const bool batched = (mode & 0xFu) == CUBOID_MODE_BATCHED;
   const LaunchShape L = launch_shape(r->t, steps);
   cudaError_t e = sieve_set_smem_limit(steps, L.smem);
@@ -240,7 +242,9 @@ static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, c
     e = launch_plan(d_ranges, i, 1, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs, r->t->n, L.target_tiles, s,
                     i == 0, L.row_lanes, h_ranges ? h_ranges + i : nullptr);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i], s);
-    if (e == cudaSuccess) e = launch_sieve(sieve_args(r, L, i, 1), steps, L.blocks, L.threads, L.smem, s, !timed);
+    SieveArgs sa = sieve_args(r, L, i, 1);
+    if (stage_fail) sa.stage_spins = 0;
+    if (e == cudaSuccess) e = launch_sieve(sa, steps, L.blocks, L.threads, L.smem, s, !timed);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i + 1], s);
   }
   if (e == cudaSuccess) e = launch_verify(verify_args(r), verify_blocks(r->t), s, !timed);
@@ -350,8 +354,10 @@ int sieve_into(cuboid_result* r, const cuboid_range* ranges, uint32_t n, uint32_
   if (!r) return CUBOID_EINVAL;
   if (!r->t) return CUBOID_ENOTABLES;
   if (r->host_only || !ranges || n == 0 || n > r->max_ranges) return CUBOID_EINVAL;
-  if ((mode & ~(0xFu | CUBOID_MODE_COUNT_STEPS | CUBOID_MODE_TIME_SIEVE)) || (mode & 0xFu) > CUBOID_MODE_BATCHED)
+  if ((mode & ~(0xFu | CUBOID_MODE_COUNT_STEPS | CUBOID_MODE_TIME_SIEVE | CUBOID_MODE_STAGE_TIMEOUT)) ||
+      (mode & 0xFu) > CUBOID_MODE_BATCHED)
     return CUBOID_EINVAL;
+  if ((mode & CUBOID_MODE_STAGE_TIMEOUT) && (mode & 0xFu) != CUBOID_MODE_PLAIN) return CUBOID_EINVAL;
   if (check_device(r) != CUBOID_OK) return CUBOID_EINVAL;
   cudaError_t e = cudaSuccess;
   const bool batched = (mode & 0xFu) == CUBOID_MODE_BATCHED;

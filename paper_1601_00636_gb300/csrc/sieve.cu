@@ -69,7 +69,6 @@ __device__ __forceinline__ void flush_counts(WarpState& ws, uint32_t* wcnt, cons
   __syncwarp();
 }
 
-constexpr uint32_t kStageSpins = 1u << 22;  // mbarrier polls before a staging time-out
 
 // Poll an mbarrier phase at most `spins` times (each poll may suspend the thread for a
 // short, hardware-chosen time); true once the phase has completed.
@@ -260,7 +259,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   for (uint32_t i = threadIdx.x; i < warps * n; i += blockDim.x) s_cnt_all[i] = 0;
   // bounded wait for the staging: on time-out the CTA records it and leaves once its
   // copies have landed (or a second bounded wait ends)
-  const bool staged = mbar_wait_parity(bar, 0u, kStageSpins);
+  const bool staged = mbar_wait_parity(bar, 0u, a.stage_spins);
   if (__syncthreads_or(!staged)) {
     pdl_wait();
     if (threadIdx.x == 0) atomicOr(&a.hdr->status, kStatusStageTimeout);

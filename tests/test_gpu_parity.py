@@ -543,3 +543,22 @@ def test_deep_primes_near_eq_2_7_bound(cb, stream):
             _check_against(got, want)
     finally:
         cb.cuboid_tables_free(t)
+
+
+def test_staging_wait_gives_up_and_reports(cb, stream, c1_tables):
+    """Failure detection without a fault: with CUBOID_MODE_STAGE_TIMEOUT every CTA's
+    bounded wait for its shared-memory staging gives up at once; the run reports
+    ETIMEOUT, and the next run on the same result and context is exact again."""
+    rng = [W.triangle(2000)]
+    res = cb.cuboid_result_create(c1_tables, 1)
+    try:
+        cb.cuboid_sieve_into(res, rng, cb.MODE_PLAIN | cb.MODE_STAGE_TIMEOUT, stream)
+        assert cb.cuboid_result_wait(res) == cb.ETIMEOUT
+        with pytest.raises(cb.CuboidError):
+            cb.cuboid_sieve_into(res, rng, cb.MODE_BATCHED | cb.MODE_STAGE_TIMEOUT, stream)
+        cb.cuboid_sieve_into(res, rng, cb.MODE_PLAIN, stream)
+        assert cb.cuboid_result_wait(res) == cb.OK
+        got = cb.cuboid_result_get(res, 0, 24)
+    finally:
+        cb.cuboid_result_free(res)
+    _check_against([got], O.run(W.first_odd_primes(24), rng)["ranges"])
