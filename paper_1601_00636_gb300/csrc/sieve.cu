@@ -485,12 +485,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     const uint32_t emask = has2 ? 0xAAAAAAAAu : FULL;  // x even: y0 is even, so even y sit at even bits
     const uint32_t nit = live ? (wend - wbeg) / G + 1 : 0u;  // words of this lane's group, per lane
     const uint32_t maxit = G == 32 ? nit : __reduce_max_sync(FULL, nit);
-    uint32_t wb = wbeg;
-    for (uint32_t j = 0; j < maxit; ++j, wb += G) {
-      const uint32_t w = wb + gl;
-      const uint32_t y0 = w << 6;
-      uint32_t al = 0, ah = 0;
-      if (j < nit && w <= wend) {
+    // one word's alive mask: range edges, coprimality (odd factors; even y when x is
+    // even), diagonal; the factor offsets advance to the lane's next word
+    auto word_mask = [&](uint32_t w, bool on, uint32_t& al, uint32_t& ah) {
+      al = 0;
+      ah = 0;
+      if (on) {
         unsigned long long rm = FULL64;
         if (w == wlo) rm &= lo_mask;
         if (w == whi) rm &= hi_mask;
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         }
         for (uint32_t i = kFacRegs; i < nfo; ++i) {
           const uint4 fc = s_fac[i];
-          const uint32_t s = mod_min(y0, fc.x, s_fmag[i]);
+          const uint32_t s = mod_min(w << 6, fc.x, s_fmag[i]);
           const uint32_t t = s ? fc.x - s : 0u;
           const uint2 mk = s_mtab[fc.z + min(t, fc.w)];
           ml |= mk.x;
@@ -526,21 +526,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         tile_pairs += __popc(al) + __popc(ah);
         if (kSteps) st_words += (al | ah) ? 1 : 0;
       }
-      // hot primes: no early-exit test
-#pragma unroll
-      for (int h = 0; h < K; ++h) {
-        if (kSteps) st_wsteps += (al | ah) ? 1 : 0;
-        const uint32_t s = sh[h];
-        const uint32_t sn = s + a.hot_step[h];  // next word: + (64 G) mod r, below 2r
-        sh[h] = min(sn, sn - a.hot_r[h]);
-        const uint32_t* tp = s_tab + rb[h] + (s >> 5);
-        const uint32_t w0 = tp[0], w1 = tp[1], w2 = tp[2];
-        al &= ~__funnelshift_r(w0, w1, s);  // the window of u_r(x mod r, y0 mod r ...)
-        ah &= ~__funnelshift_r(w1, w2, s);
-        hs[h] += __popc(al) + __popc(ah);
-      }
-      if (kSteps) st_warpsteps += K;
-      // queue the words still alive
+    };
+    // queue the lanes' words still alive and finish full batches of 32 through the rest
+    // of the primes
+    auto enqueue = [&](uint32_t al, uint32_t ah, uint32_t y0) {
       const uint32_t bal = __ballot_sync(FULL, (al | ah) != 0u);
       if (bal) {
         if (al | ah) s_queue[qn + __popc(bal & lanemask_lt)] = make_uint4(x, y0, al, ah);
@@ -549,6 +538,37 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         drain<kSteps>(a, s_info, s_tab, wcnt, s_queue, qn, K, rows_q, k, lane, ws, st_wsteps, st_warpsteps,
                       false);
       }
+    };
+    // two words a lane per iteration (G words apart), whose hot-prime chains interleave
+    uint32_t wb = wbeg;
+    for (uint32_t j = 0; j < maxit; j += 2, wb += 2 * G) {
+      const uint32_t wA = wb + gl, wB = wA + G;
+      uint32_t alA, ahA, alB, ahB;
+      word_mask(wA, j < nit && wA <= wend, alA, ahA);
+      word_mask(wB, j + 1 < nit && wB <= wend, alB, ahB);
+      // hot primes: no early-exit test
+#pragma unroll
+      for (int h = 0; h < K; ++h) {
+        if (kSteps) st_wsteps += ((alA | ahA) ? 1 : 0) + ((alB | ahB) ? 1 : 0);
+        const uint32_t r = a.hot_r[h], step = a.hot_step[h];  // step = (64 G) mod r
+        const uint32_t sA = sh[h];
+        const uint32_t t1 = sA + step;
+        const uint32_t sB = min(t1, t1 - r);
+        const uint32_t t2 = sB + step;
+        sh[h] = min(t2, t2 - r);
+        const uint32_t* pA = s_tab + rb[h] + (sA >> 5);
+        const uint32_t* pB = s_tab + rb[h] + (sB >> 5);
+        const uint32_t a0 = pA[0], a1 = pA[1], a2 = pA[2];
+        const uint32_t b0 = pB[0], b1 = pB[1], b2 = pB[2];
+        alA &= ~__funnelshift_r(a0, a1, sA);  // the window of u_r(x mod r, y0 mod r ...)
+        ahA &= ~__funnelshift_r(a1, a2, sA);
+        alB &= ~__funnelshift_r(b0, b1, sB);
+        ahB &= ~__funnelshift_r(b1, b2, sB);
+        hs[h] += __popc(alA) + __popc(ahA) + __popc(alB) + __popc(ahB);
+      }
+      if (kSteps) st_warpsteps += (j + 1 < maxit) ? 2 * K : K;
+      enqueue(alA, ahA, wA << 6);
+      enqueue(alB, ahB, wB << 6);
     }
     if constexpr (K > 0) {
       if ((uint32_t)(K - 1) > ws.imax) ws.imax = (uint32_t)(K - 1);
