@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcuboid.so")
@@ -296,17 +297,30 @@ def cuboid_result_wait(res) -> int:
     return st
 
 
+_GET_BUFS = threading.local()  # per thread: output buffers of cuboid_result_get, by n_primes
+
+
+def _get_bufs(n_primes: int):
+    cache = getattr(_GET_BUFS, "by_n", None)
+    if cache is None:
+        cache = _GET_BUFS.by_n = {}
+    b = cache.get(n_primes)
+    if b is None:
+        npairs, ns, nr = _u64(), _u64(), _u64()
+        counts = (_u64 * n_primes)()
+        sp, rp = C.POINTER(_u64)(), C.POINTER(cuboid_root)()
+        b = cache[n_primes] = (npairs, counts, ns, sp, nr, rp,
+                               (C.byref(npairs), counts, C.byref(ns), C.byref(sp), C.byref(nr), C.byref(rp)))
+    return b
+
+
 def cuboid_result_get(res, range_idx: int, n_primes: int) -> dict:
-    npairs, ns, nr = _u64(), _u64(), _u64()
-    counts = (_u64 * n_primes)()
-    sp = C.POINTER(_u64)()
-    rp = C.POINTER(cuboid_root)()
-    _check(_lib.cuboid_result_get(res, range_idx, C.byref(npairs), counts, C.byref(ns), C.byref(sp),
-                                  C.byref(nr), C.byref(rp)), "cuboid_result_get")
+    npairs, counts, ns, sp, nr, rp, args = _get_bufs(n_primes)
+    _check(_lib.cuboid_result_get(res, range_idx, *args), "cuboid_result_get")
     surv = [(int(sp[i]) >> 32, int(sp[i]) & 0xFFFFFFFF) for i in range(ns.value)]
     roots = [(rp[i].p, rp[i].q, (int(rp[i].t_hi) << 64) | int(rp[i].t_lo)) for i in range(nr.value)]
     cuboids = [rt for rt, f in zip(roots, cuboid_theorem11_flags(roots)) if f] if roots else []
-    return {"n_pairs": npairs.value, "counts": list(counts), "survivors": surv, "roots": roots,
+    return {"n_pairs": npairs.value, "counts": counts[:], "survivors": surv, "roots": roots,
             "cuboids": cuboids}
 
 
