@@ -308,8 +308,9 @@ int cuboid_sieve_noalloc(const cuboid_tables* t, const cuboid_range* ranges_dev,
 
 /* The region of Theorem 1.2 (Eq. 1.2): min(cbrt(p/9), p/59) <= q <= 59 p; for p >= 152
  * it is the segment of Eq. 5.2, cbrt(p/9) <= q <= 59 p.  A scan walks the rows p upward,
- * each row over its segment, in batches of 100 rows (the granularity of the paper's
- * Get_current_p), sieving coprime q != p. */
+ * each row over its segment, sieving coprime q != p, in batches aligned to hundreds of p:
+ * 100 rows for the asynchronous search (the granularity of the paper's Get_current_p),
+ * up to 2000 rows, two batches in flight, for the synchronous scan. */
 typedef struct cuboid_search_report {
   uint32_t p, q;      /* where a resumed scan starts: the next row and its first q */
   uint32_t r_max;     /* deepest prime needed (last rejecting prime in the effective order

@@ -31,6 +31,7 @@ namespace {
 
 constexpr uint32_t kPMax = 72796055u;   // 59 p stays below 2^32 (section 5)
 constexpr uint32_t kBatchRows = 100;     // the granularity of the paper's progress probe
+constexpr uint32_t kScanRows = 2000;     // rows per batch of the synchronous scan
 constexpr uint32_t kFirstSearchP = 152;  // Eq. 5.2 holds from here on (section 5)
 
 // Smallest q >= 1 with q >= min(cbrt(p/9), p/59), in integers: 9 q^3 >= p or 59 q >= p.
@@ -65,26 +66,34 @@ void deepest(const cuboid_tables* t, const std::vector<uint64_t>& counts, uint64
   *r_max = d ? t->info[d - 1].r : 0;
 }
 
-// Sieve rows [p, p_end] (row p from q0 on) as one batched launch; add into `tot` and
-// `batch` (this batch alone).  keep_records: append survivor and root records.
-int scan_batch(cuboid_result* res, const cuboid_tables* t, uint32_t p, uint32_t q0, uint32_t p_end,
-               cudaStream_t s, Totals& tot, std::vector<uint64_t>& batch_counts, uint64_t& batch_surv) {
+// Enqueue rows [p, p_end] (row p from q0 on) as one batched launch on res (results copied
+// back in stream order); *n_ranges receives the number of row ranges.
+int scan_submit(cuboid_result* res, uint32_t p, uint32_t q0, uint32_t p_end, cudaStream_t s,
+                uint32_t* n_ranges) {
   std::vector<cuboid_range> rg;
+  rg.reserve(p_end - p + 1);
   for (uint64_t x = p; x <= p_end; ++x) {
     const uint32_t lo = x == p ? std::max(q0, qmin((uint32_t)x)) : qmin((uint32_t)x);
     const uint32_t hi = (uint32_t)(59ull * x);
     if (lo > hi) continue;
     rg.push_back(cuboid_range{(uint32_t)x, (uint32_t)x, lo, hi, 0u, 0u});
   }
+  *n_ranges = (uint32_t)rg.size();
+  if (rg.empty()) return CUBOID_OK;
+  return sieve_into(res, rg.data(), (uint32_t)rg.size(), CUBOID_MODE_BATCHED, s, false, true);
+}
+
+// Wait for a submitted batch and add it into `tot` and `batch_counts` / `batch_surv` (this
+// batch alone).  Returns OK, EOVERFLOW (records capped; counts exact) or an error.
+int scan_collect(cuboid_result* res, const cuboid_tables* t, uint32_t n_ranges, Totals& tot,
+                 std::vector<uint64_t>& batch_counts, uint64_t& batch_surv) {
   batch_counts.assign(t->n, 0);
   batch_surv = 0;
-  if (rg.empty()) return CUBOID_OK;
-  int st = sieve_into(res, rg.data(), (uint32_t)rg.size(), CUBOID_MODE_BATCHED, s, false, true);
-  if (st != CUBOID_OK) return st;
-  st = result_wait(res);
+  if (n_ranges == 0) return CUBOID_OK;
+  const int st = result_wait(res);
   if (st != CUBOID_OK && st != CUBOID_EOVERFLOW) return st;
   std::vector<uint64_t> c(t->n);
-  for (uint32_t k = 0; k < rg.size(); ++k) {
+  for (uint32_t k = 0; k < n_ranges; ++k) {
     uint64_t np = 0, ns = 0, nr = 0;
     const uint64_t* sv = nullptr;
     const cuboid_root* rv = nullptr;
@@ -101,6 +110,15 @@ int scan_batch(cuboid_result* res, const cuboid_tables* t, uint32_t p, uint32_t 
   return st;
 }
 
+// Sieve rows [p, p_end] (row p from q0 on) as one batched launch and add the results.
+int scan_batch(cuboid_result* res, const cuboid_tables* t, uint32_t p, uint32_t q0, uint32_t p_end,
+               cudaStream_t s, Totals& tot, std::vector<uint64_t>& batch_counts, uint64_t& batch_surv) {
+  uint32_t nr = 0;
+  const int st = scan_submit(res, p, q0, p_end, s, &nr);
+  if (st != CUBOID_OK) return st;
+  return scan_collect(res, t, nr, tot, batch_counts, batch_surv);
+}
+
 int check_start(const cuboid_tables* t, uint32_t p, uint32_t q, bool search) {
   if (!t) return CUBOID_ENOTABLES;
   if (p == 0 || (search && p < kFirstSearchP)) return CUBOID_ERANGE;
@@ -113,9 +131,10 @@ int check_start(const cuboid_tables* t, uint32_t p, uint32_t q, bool search) {
 
 }  // namespace
 
-// Last row of the hundred that holds p (batches are aligned to hundreds of p).
-static uint32_t batch_end(uint32_t p, uint32_t p_to) {
-  const uint64_t e = (uint64_t)p / kBatchRows * kBatchRows + kBatchRows - 1;
+// Last row of a batch of `rows` rows starting in the hundred that holds p (batches are
+// aligned to hundreds of p).
+static uint32_t batch_end(uint32_t p, uint32_t p_to, uint32_t rows = kBatchRows) {
+  const uint64_t e = (uint64_t)p / kBatchRows * kBatchRows + rows - 1;
   return (uint32_t)std::min<uint64_t>(e, p_to);
 }
 
@@ -142,27 +161,45 @@ extern "C" int cuboid_region_scan(cuboid_tables* t, uint32_t p_from, uint32_t q_
   if (p_to < p_from) return CUBOID_ERANGE;
   if (p_to > kPMax) return CUBOID_EPMAX;
   cudaStream_t s = (cudaStream_t)stream;
-  cuboid_result* res = nullptr;
-  st = result_create(t, kBatchRows, 1ull << 16, 1ull << 12, &res);
-  if (st != CUBOID_OK) return st;
+  // Two result objects: the next batch is sieved while the host adds up the last one.
+  cuboid_result* res[2] = {nullptr, nullptr};
+  st = result_create(t, kScanRows, 1ull << 16, 1ull << 12, &res[0]);
+  if (st == CUBOID_OK) st = result_create(t, kScanRows, 1ull << 16, 1ull << 12, &res[1]);
+  if (st != CUBOID_OK) {
+    if (res[0]) cuboid_result_free(res[0]);
+    return st;
+  }
   Totals tot;
   tot.counts.assign(t->n, 0);
   std::vector<uint64_t> bc;
   uint64_t bs = 0;
   bool overflow = false;
-  uint32_t p = p_from, q0 = q_from;
-  while (true) {
-    const uint32_t e = batch_end(p, p_to);
-    st = scan_batch(res, t, p, q0, e, s, tot, bc, bs);
-    if (st == CUBOID_EOVERFLOW) {
-      overflow = true;
-      st = CUBOID_OK;
+  uint32_t n_in[2] = {0, 0};
+  uint32_t e = batch_end(p_from, p_to, kScanRows);
+  st = scan_submit(res[0], p_from, q_from, e, s, &n_in[0]);
+  int cur = 0;
+  while (st == CUBOID_OK) {
+    const bool more = e < p_to;
+    uint32_t e2 = e;
+    if (more) {
+      e2 = batch_end(e + 1, p_to, kScanRows);
+      st = scan_submit(res[cur ^ 1], e + 1, 0, e2, s, &n_in[cur ^ 1]);
     }
-    if (st != CUBOID_OK || e >= p_to) break;
-    p = e + 1;
-    q0 = 0;
+    const int sc = scan_collect(res[cur], t, n_in[cur], tot, bc, bs);
+    if (sc == CUBOID_EOVERFLOW) {
+      overflow = true;
+    } else if (sc != CUBOID_OK && st == CUBOID_OK) {
+      st = sc;
+    }
+    if (!more || st != CUBOID_OK) break;
+    cur ^= 1;
+    e = e2;
   }
-  cuboid_result_free(res);
+  // a batch still in flight after an error is waited for before its buffers go
+  for (int k = 0; k < 2; ++k) {
+    result_wait(res[k]);
+    cuboid_result_free(res[k]);
+  }
   if (st != CUBOID_OK) return st;
   if (counts) std::memcpy(counts, tot.counts.data(), t->n * sizeof(uint64_t));
   if (surv) std::memcpy(surv, tot.surv.data(), std::min<uint64_t>(surv_cap, tot.surv.size()) * sizeof(uint64_t));

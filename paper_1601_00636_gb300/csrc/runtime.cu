@@ -12,10 +12,12 @@ namespace cuboid {
 
 constexpr uint64_t kDefaultSurvCap = 1ull << 20;
 constexpr uint64_t kDefaultRootCap = 1ull << 16;
-constexpr uint32_t kDefaultThreads = 512;
+// default shape: the one the autotuner picks most often on this part (two 256-thread CTAs
+// per SM with the 128-register build, six hot primes)
+constexpr uint32_t kDefaultThreads = 256;
 constexpr uint32_t kDefaultCtasPerSm = 2;
 constexpr uint32_t kDefaultTilesPerWarp = 3;
-constexpr uint32_t kDefaultHot = 5;
+constexpr uint32_t kDefaultHot = 6;
 constexpr size_t kDefaultTableSmem = 48 * 1024;
 
 }  // namespace cuboid

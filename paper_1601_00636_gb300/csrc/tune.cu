@@ -152,7 +152,7 @@ extern "C" int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uin
     return CUBOID_OK;
   };
 
-  cuboid_tuning cur{512, 2, 0, 3, 5, 32};
+  cuboid_tuning cur{256, 2, 0, 3, 6, 32};
   float cur_ms = 0.f;
   st = measure(cur, &cur_ms);
   const uint32_t hots[] = {2, 4, 5, 6};
@@ -177,11 +177,18 @@ extern "C" int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uin
       }
     };
     try_dim([](cuboid_tuning& c, uint32_t v) { c.hot_primes = v; }, hots, 4);
-    try_dim([](cuboid_tuning& c, uint32_t v) { c.tiles_per_warp = v; }, tpws, 8);
+    // lanes per row and tiles per warp interact (both set how rows split into subtiles):
+    // swept jointly
+    for (int li = 0; li < 3 && st == CUBOID_OK && !mismatch; ++li) {
+      const uint32_t lane_v = lanes[li];
+      try_dim([lane_v](cuboid_tuning& c, uint32_t v) {
+        c.row_lanes = lane_v;
+        c.tiles_per_warp = v;
+      }, tpws, 8);
+    }
     try_dim([](cuboid_tuning& c, uint32_t v) { c.block_threads = v; }, thr, 2);
     try_dim([](cuboid_tuning& c, uint32_t v) { c.ctas_per_sm = v; }, ctas, 3);
     try_dim([](cuboid_tuning& c, uint32_t v) { c.smem_primes = v; }, smemp, 4);
-    try_dim([](cuboid_tuning& c, uint32_t v) { c.row_lanes = v; }, lanes, 3);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
