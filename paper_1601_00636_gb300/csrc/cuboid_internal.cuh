@@ -81,6 +81,56 @@ constexpr unsigned kStatusStageTimeout = 16u;  // a CTA's shared-memory staging 
 
 // Odd trial-division primes below 2^16 with the exact-divisibility constants
 // inv = f^-1 mod 2^32 and lim = floor((2^32 - 1) / f):  f | n  <=>  n * inv <= lim.
+// ---- planning of one range (shared by the plan kernel and the single-range sieve)
+
+// Orientation and word count of a range: rows of p, or of q when the rectangle is narrow
+// in q (or forced by the flags).  Returns false for an invalid range (P is then empty).
+__host__ __device__ inline bool plan_orient(const cuboid_range& R, TilePlan& P, unsigned long long& words) {
+  const uint32_t fl = R.flags;
+  const bool bad = R.p_lo == 0 || R.q_lo == 0 || R.p_lo > R.p_hi || R.q_lo > R.q_hi || R.reserved != 0 ||
+                   (fl & ~0xFu) || ((fl & CUBOID_ROWS_P) && (fl & CUBOID_ROWS_Q));
+  P.chunk_words = 1;
+  P.tile_end = 0;
+  words = 0;
+  if (bad) {
+    P.x_lo = 1;
+    P.x_hi = 0;
+    P.y_lo = 1;
+    P.y_hi = 0;
+    P.flags = 0;
+    return false;
+  }
+  const bool rows_q = (fl & CUBOID_ROWS_Q) || (!(fl & CUBOID_ROWS_P) && (R.p_hi - R.p_lo) > (R.q_hi - R.q_lo));
+  P.x_lo = rows_q ? R.q_lo : R.p_lo;
+  P.x_hi = rows_q ? R.q_hi : R.p_hi;
+  P.y_lo = rows_q ? R.p_lo : R.q_lo;
+  P.y_hi = rows_q ? R.p_hi : R.q_hi;
+  P.flags = (fl & (CUBOID_Q_LT_P | CUBOID_ALLOW_DIAGONAL)) | (rows_q ? kRowsQ : 0u);
+  words = ((unsigned long long)(P.x_hi - P.x_lo) + 1) * ((P.y_hi >> 6) - (P.y_lo >> 6) + 1);
+  return true;
+}
+
+// Words per subtile from the total words of a launch and its target number of tiles.
+__host__ __device__ inline unsigned long long plan_chunk(unsigned long long total_words, uint32_t target_tiles,
+                                                         uint32_t subtiles_per_tile) {
+  const unsigned long long target_sub = (unsigned long long)(target_tiles ? target_tiles : 1) * subtiles_per_tile;
+  unsigned long long cw = (total_words + target_sub - 1) / target_sub;
+  if (cw < 1) cw = 1;
+  if (cw > kMaxChunkWords) cw = kMaxChunkWords;
+  return cw;
+}
+
+// Sets P.chunk_words and returns the range's tiles (subtiles_per_tile subtiles each).
+__host__ __device__ inline unsigned long long plan_tiles(TilePlan& P, unsigned long long cw,
+                                                         uint32_t subtiles_per_tile) {
+  if (P.x_lo > P.x_hi) return 0;
+  const unsigned long long nw = (P.y_hi >> 6) - (P.y_lo >> 6) + 1;
+  const unsigned long long chunk = nw < cw ? nw : cw;
+  P.chunk_words = (uint32_t)chunk;
+  const unsigned long long subtiles = ((unsigned long long)(P.x_hi - P.x_lo) + 1) * ((nw + chunk - 1) / chunk);
+  return (subtiles + subtiles_per_tile - 1) / subtiles_per_tile;
+}
+
 struct TrialPrime {
   uint32_t f, inv, lim, pad;
 };
@@ -137,6 +187,13 @@ struct SieveArgs {
   uint32_t hot_step[8];          // (64 row_lanes) mod r: a lane's stride between words
   uint32_t row_lanes;            // lanes per row (8, 16, 32)
   uint32_t stage_spins;          // polls of the staging barrier before a time-out
+  // Single-range launch without a plan kernel (self_plan = 1): every CTA plans the range
+  // itself (read from self_range, or self_range_val when that is null) for target_tiles
+  // tiles; the header, counts and pair total start at zero (the previous run cleared them).
+  uint32_t self_plan = 0;
+  uint32_t target_tiles = 0;
+  const cuboid_range* self_range = nullptr;
+  cuboid_range self_range_val = {};
   uint32_t n_sms;               // SMs of the device (picks the register budget of the variant)
 };
 constexpr uint32_t kMaxHot = 8;
@@ -149,6 +206,8 @@ struct VerifyArgs {
   cuboid_root* roots;
   uint32_t* root_range;
   unsigned long long root_cap;
+  unsigned long long* zero_block = nullptr;  // cleared by block 0 after the sieve (may be null)
+  uint32_t zero_words = 0;
 };
 
 // Launchers (each checks its own launch and returns cudaError_t).

@@ -54,30 +54,10 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
   TilePlan P_first{};  // this thread's first range, kept for the scan below
   for (uint32_t k = tid; k < count; k += blockDim.x) {
     const cuboid_range R = use_inl ? inl : ranges[first + k];  // inl: one range passed by value
-    const uint32_t fl = R.flags;
-    const bool bad = R.p_lo == 0 || R.q_lo == 0 || R.p_lo > R.p_hi || R.q_lo > R.q_hi ||
-                     R.reserved != 0 || (fl & ~0xFu) ||
-                     ((fl & CUBOID_ROWS_P) && (fl & CUBOID_ROWS_Q));
     TilePlan P;
-    if (bad) {
-      atomicOr(&hdr->status, kStatusBadRange);
-      P.x_lo = 1;
-      P.x_hi = 0;
-      P.y_lo = 1;
-      P.y_hi = 0;
-      P.flags = 0;
-    } else {
-      const bool rows_q = (fl & CUBOID_ROWS_Q) ||
-                          (!(fl & CUBOID_ROWS_P) && (R.p_hi - R.p_lo) > (R.q_hi - R.q_lo));
-      P.x_lo = rows_q ? R.q_lo : R.p_lo;
-      P.x_hi = rows_q ? R.q_hi : R.p_hi;
-      P.y_lo = rows_q ? R.p_lo : R.q_lo;
-      P.y_hi = rows_q ? R.p_hi : R.q_hi;
-      P.flags = (fl & (CUBOID_Q_LT_P | CUBOID_ALLOW_DIAGONAL)) | (rows_q ? kRowsQ : 0u);
-      my_words += ((unsigned long long)(P.x_hi - P.x_lo) + 1) * ((P.y_hi >> 6) - (P.y_lo >> 6) + 1);
-    }
-    P.chunk_words = 1;
-    P.tile_end = 0;
+    unsigned long long words;
+    if (!plan_orient(R, P, words)) atomicOr(&hdr->status, kStatusBadRange);
+    my_words += words;
     if (k == tid) P_first = P;
     else plan[first + k] = P;
   }
@@ -85,10 +65,7 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
   if (lane == 0 && my_words) atomicAdd(&s_words, my_words);
   __syncthreads();
   // chunk size from the target number of subtiles (a tile is subtiles_per_tile of them)
-  const unsigned long long target_sub = (unsigned long long)(target_tiles ? target_tiles : 1) * subtiles_per_tile;
-  unsigned long long cw = (s_words + target_sub - 1) / target_sub;
-  if (cw < 1) cw = 1;
-  if (cw > kMaxChunkWords) cw = kMaxChunkWords;
+  const unsigned long long cw = plan_chunk(s_words, target_tiles, subtiles_per_tile);
 
   for (uint32_t base = 0; base < count; base += blockDim.x) {
     const uint32_t k = base + tid;
@@ -96,13 +73,7 @@ __global__ void __launch_bounds__(1024) k_plan(const cuboid_range* ranges, uint3
     TilePlan P;
     if (k < count) {
       P = base == 0 ? P_first : plan[first + k];
-      if (P.x_lo <= P.x_hi) {
-        const unsigned long long nw = (P.y_hi >> 6) - (P.y_lo >> 6) + 1;
-        const unsigned long long chunk = nw < cw ? nw : cw;
-        P.chunk_words = (uint32_t)chunk;
-        const unsigned long long subtiles = ((unsigned long long)(P.x_hi - P.x_lo) + 1) * ((nw + chunk - 1) / chunk);
-        tiles = (subtiles + subtiles_per_tile - 1) / subtiles_per_tile;
-      }
+      tiles = plan_tiles(P, cw, subtiles_per_tile);
     }
     // block inclusive scan of tiles
     unsigned long long v = tiles;

@@ -29,8 +29,14 @@ struct cuboid_result {
   int device = 0;
   uint32_t max_ranges = 0;
   uint64_t surv_cap = 0, root_cap = 0;
-  // device: header, pair totals and counts share one block (one copy brings them back)
-  unsigned char* d_block = nullptr;
+  // device: header, pair totals and counts share one block (one copy brings them back).
+  // Two blocks: a plain single-range run on a one-range result works in the block the
+  // last run did not use, which that run's root-test kernel cleared, so it needs no plan
+  // kernel; other runs reset the current block with the plan kernel.
+  unsigned char* d_blocks[2] = {nullptr, nullptr};
+  unsigned char* d_block = nullptr;  // the current one
+  size_t block_bytes = 0;
+  int cur = 0;
   unsigned char* h_block = nullptr;  // its pinned host mirror
   DevHeader* d_hdr = nullptr;
   cuboid_range* d_ranges = nullptr;
@@ -48,8 +54,8 @@ struct cuboid_result {
   unsigned long long* h_npairs = nullptr;
   cudaEvent_t done = nullptr;
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t graph[4] = {};     // [count_steps + 2 * time_sieve]
-  cuboid_tuning graph_tuning[4] = {};  // tuning each graph was captured with
+  cudaGraphExec_t graph[8] = {};     // [count_steps + 2 * time_sieve + 4 * current block]
+  cuboid_tuning graph_tuning[8] = {};  // tuning each graph was captured with
   // last run
   uint32_t n_ranges = 0;
   bool downloaded = false;
@@ -69,9 +75,19 @@ struct cuboid_result {
 
 namespace cuboid {
 
+constexpr size_t kHdrBytes = (sizeof(DevHeader) + 63) / 64 * 64;  // header padded to 128 B
+
+// Point the header, pair-total and count pointers at block b.
+static void use_block(cuboid_result* r, int b) {
+  r->cur = b;
+  r->d_block = r->d_blocks[b];
+  r->d_hdr = reinterpret_cast<DevHeader*>(r->d_block);
+  r->d_npairs = reinterpret_cast<unsigned long long*>(r->d_block + kHdrBytes);
+  r->d_counts = r->d_npairs + r->max_ranges;
+}
+
 // Result block: the device header (padded to 64 bytes), then max_ranges pair totals, then
 // the counts of as many ranges as a run fills.
-constexpr size_t kHdrBytes = (sizeof(DevHeader) + 63) / 64 * 64;
 static size_t result_block_bytes(uint32_t max_ranges, size_t n_counts) {
   return kHdrBytes + (size_t)max_ranges * sizeof(unsigned long long) + n_counts * sizeof(unsigned long long);
 }
@@ -156,7 +172,7 @@ static SieveArgs sieve_args(cuboid_result* r, const LaunchShape& L, uint32_t fir
   return a;
 }
 
-static VerifyArgs verify_args(cuboid_result* r) {
+static VerifyArgs verify_args(cuboid_result* r, bool clear_other) {
   VerifyArgs v;
   v.surv = r->d_surv;
   v.surv_range = r->d_surv_range;
@@ -165,6 +181,10 @@ static VerifyArgs verify_args(cuboid_result* r) {
   v.roots = r->d_roots;
   v.root_range = r->d_root_range;
   v.root_cap = r->root_cap;
+  if (clear_other) {
+    v.zero_block = reinterpret_cast<unsigned long long*>(r->d_blocks[r->cur ^ 1]);
+    v.zero_words = (uint32_t)(r->block_bytes / 8);
+  }
   return v;
 }
 
@@ -192,7 +212,7 @@ static cudaError_t enqueue_batched(cuboid_result* r, const LaunchShape& L, bool 
   if (e == cudaSuccess)
     e = launch_sieve(sieve_args(r, L, 0, 0xFFFFFFFFu), steps, L.blocks, L.threads, L.smem, s, !timed);
   if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(r->tev[1], s, cudaEventRecordExternal);
-  if (e == cudaSuccess) e = launch_verify(verify_args(r), verify_blocks(r->t), s, !timed);
+  if (e == cudaSuccess) e = launch_verify(verify_args(r, false), verify_blocks(r->t), s, !timed);
   return e;
 }
 
@@ -216,7 +236,7 @@ static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, c
   if (batched) {
     e = launch_reset(r->d_hdr, n, s);  // zero the header, n_ranges = n
     if (e != cudaSuccess) return e;
-    const int gi = (steps ? 1 : 0) + (timed ? 2 : 0);
+    const int gi = (steps ? 1 : 0) + (timed ? 2 : 0) + 4 * r->cur;  // graphs hold the block's address
     cudaGraphExec_t& g = r->graph[gi];
     if (g && std::memcmp(&r->graph_tuning[gi], &r->t->tuning, sizeof(cuboid_tuning)) != 0) {
       cudaGraphExecDestroy(g);
@@ -240,6 +260,24 @@ static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, c
     }
     return cudaGraphLaunch(g, s);
   }
+  if (n == 1 && r->max_ranges == 1) {
+    // One range on a one-range result: no plan kernel.  The run works in the block the
+    // last run did not use (cleared by that run's root test), every CTA plans the range
+    // itself, and this run's root test clears the other block for the next run.
+    use_block(r, r->cur ^ 1);
+    SieveArgs sa = sieve_args(r, L, 0, 1);
+    sa.self_plan = 1;
+    sa.target_tiles = L.target_tiles;
+    sa.self_range = h_ranges ? nullptr : d_ranges;
+    if (h_ranges) sa.self_range_val = h_ranges[0];
+    if (stage_fail) sa.stage_spins = 0;
+    if (timed) e = cudaEventRecord(r->tev[0], s);
+    if (e == cudaSuccess) e = launch_sieve(sa, steps, L.blocks, L.threads, L.smem, s, false);
+    if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[1], s);
+    if (e == cudaSuccess) e = launch_verify(verify_args(r, true), verify_blocks(r->t), s, !timed);
+    if (timed) r->timed_launches = 1;
+    return e;
+  }
   for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
     e = launch_plan(d_ranges, i, 1, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs, r->t->n, L.target_tiles, s,
                     i == 0, L.row_lanes, h_ranges ? h_ranges + i : nullptr);
@@ -249,7 +287,7 @@ static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, c
     if (e == cudaSuccess) e = launch_sieve(sa, steps, L.blocks, L.threads, L.smem, s, !timed);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i + 1], s);
   }
-  if (e == cudaSuccess) e = launch_verify(verify_args(r), verify_blocks(r->t), s, !timed);
+  if (e == cudaSuccess) e = launch_verify(verify_args(r, false), verify_blocks(r->t), s, !timed);
   if (timed) r->timed_launches = n;
   return e;
 }
@@ -279,7 +317,7 @@ static void result_release(cuboid_result* r) {
     for (auto ev : r->tev) cudaEventDestroy(ev);
     if (r->cap_stream) cudaStreamDestroy(r->cap_stream);
     if (r->done) cudaEventDestroy(r->done);
-    cudaFree(r->d_block);
+    cudaFree(r->d_blocks[0]);
     cudaFree(r->d_ranges);
     cudaFree(r->d_plan);
     cudaFree(r->d_surv);
@@ -310,12 +348,13 @@ int result_create(const cuboid_tables* t, uint32_t max_ranges, uint64_t surv_cap
     e = (call);                                       \
   }
   const size_t block = result_block_bytes(max_ranges, nc);
-  AL(cudaMalloc(&r->d_block, block));
+  r->block_bytes = block;
+  AL(cudaMalloc(&r->d_blocks[0], 2 * block));
   AL(cudaMallocHost(&r->h_block, block));
+  AL(cudaMemset(r->d_blocks[0], 0, 2 * block));
   if (e == cudaSuccess) {
-    r->d_hdr = reinterpret_cast<DevHeader*>(r->d_block);
-    r->d_npairs = reinterpret_cast<unsigned long long*>(r->d_block + kHdrBytes);
-    r->d_counts = r->d_npairs + max_ranges;
+    r->d_blocks[1] = r->d_blocks[0] + block;
+    use_block(r, 0);
     r->h_hdr = reinterpret_cast<DevHeader*>(r->h_block);
     r->h_npairs = reinterpret_cast<unsigned long long*>(r->h_block + kHdrBytes);
     r->h_counts = r->h_npairs + max_ranges;

@@ -219,7 +219,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   uint32_t* s_foff = reinterpret_cast<uint32_t*>(s_mtab + kMaskTab);                       // [64]
   uint32_t* s_fmag_all = s_foff + 64;                                                       // [warps][NG][kMaxFactors]
   uint32_t* s_cnt_all = s_fmag_all + warps * NG * kMaxFactors;                              // [warps][n]
-  __shared__ __align__(8) unsigned long long s_bar;  // completion of the two bulk copies
+  __shared__ __align__(8) unsigned long long s_bar;  // completion of the bulk copies
+  __shared__ TilePlan s_self_plan;                    // the single range's plan (self_plan)
+  __shared__ unsigned long long s_self_total;
 
   const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&s_bar);
   if (threadIdx.x == 0) {
@@ -256,6 +258,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
                  "l"(a.mimg), "r"(mimg_bytes), "r"(bar)
                  : "memory");
   }
+  if (a.self_plan && threadIdx.x == 0) {
+    const cuboid_range R = a.self_range ? *a.self_range : a.self_range_val;
+    TilePlan P;
+    unsigned long long words;
+    const bool ok = plan_orient(R, P, words);
+    const unsigned long long tiles = plan_tiles(P, plan_chunk(words, a.target_tiles, NG), NG);
+    P.tile_end = tiles;
+    s_self_plan = P;
+    s_self_total = tiles;
+    if (!ok && blockIdx.x == 0) atomicOr(&a.hdr->status, kStatusBadRange);
+  }
   for (uint32_t i = threadIdx.x; i < warps * n; i += blockDim.x) s_cnt_all[i] = 0;
   // bounded wait for the staging: on time-out the CTA records it and leaves once its
   // copies have landed (or a second bounded wait ends)
@@ -273,8 +286,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   uint32_t* s_fmag = s_fmag_all + (wid * NG + g) * kMaxFactors;
   uint4* s_queue = s_queue_all + wid * kQueue;
   uint32_t* wcnt = s_cnt_all + wid * n;
-  const uint32_t count = a.range_count == kNoRange ? a.hdr->n_ranges : a.range_count;
-  const unsigned long long total = a.hdr->total_tiles;
+  const uint32_t count = a.self_plan ? 1u : (a.range_count == kNoRange ? a.hdr->n_ranges : a.range_count);
+  const unsigned long long total = a.self_plan ? s_self_total : a.hdr->total_tiles;
 
   WarpState ws{kNoRange, 0, 0, 0};
   unsigned long long st_words = 0, st_wsteps = 0, st_warpsteps = 0, st_tiles = 0;
@@ -308,7 +321,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   if (lane == 0) next = atomicAdd(&a.hdr->cursor, 1ull);
   next = __shfl_sync(FULL, next, 0);
   TilePlan P1{};  // a single-range launch reads its plan once
-  if (count == 1) P1 = a.plan[a.range_first];
+  if (a.self_plan) P1 = s_self_plan;
+  else if (count == 1) P1 = a.plan[a.range_first];
 
   for (;;) {
     const unsigned long long tile = next;

@@ -562,3 +562,34 @@ def test_staging_wait_gives_up_and_reports(cb, stream, c1_tables):
     finally:
         cb.cuboid_result_free(res)
     _check_against([got], O.run(W.first_odd_primes(24), rng)["ranges"])
+
+
+def test_single_range_result_alternating_forms(cb, stream, c1_tables):
+    """A one-range result alternates between the plan-free single-range run (two result
+    blocks, each cleared by the other run's root test) and the planned forms; every run
+    equals the oracle, including after a run whose staging gave up."""
+    import torch
+    rngs = [W.triangle(1500), W.rect(700, 900, 1, 3000), W.rect(5, 5, 1, 100000)]
+    want = [O.run(W.first_odd_primes(24), [r])["ranges"][0] for r in rngs]
+    dev = [torch.frombuffer(bytearray(bytes(cb.ranges_array([r]))), dtype=torch.uint8).cuda() for r in rngs]
+    res = cb.cuboid_result_create(c1_tables, 1)
+    try:
+        seq = [("host", cb.MODE_PLAIN), ("host", cb.MODE_BATCHED), ("dev", cb.MODE_PLAIN),
+               ("host", cb.MODE_PLAIN | cb.MODE_STAGE_TIMEOUT), ("host", cb.MODE_PLAIN),
+               ("dev", cb.MODE_BATCHED), ("host", cb.MODE_PLAIN | cb.MODE_COUNT_STEPS),
+               ("dev", cb.MODE_PLAIN | cb.MODE_TIME_SIEVE), ("host", cb.MODE_PLAIN)]
+        for i, (src, mode) in enumerate(seq):
+            k = i % 3
+            if src == "host":
+                cb.cuboid_sieve_into(res, [rngs[k]], mode, stream)
+            else:
+                cb.cuboid_sieve_device(res, dev[k].data_ptr(), 1, mode, stream)
+                cb.cuboid_result_download(res, stream)
+            st = cb.cuboid_result_wait(res)
+            if mode & cb.MODE_STAGE_TIMEOUT:
+                assert st == cb.ETIMEOUT
+                continue
+            assert st == cb.OK, (i, src, mode)
+            _check_against([cb.cuboid_result_get(res, 0, 24)], [want[k]])
+    finally:
+        cb.cuboid_result_free(res)
