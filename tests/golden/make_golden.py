@@ -1,7 +1,7 @@
 """Writes the stored expected values of the GPU parity tests.  Calls only the oracle and
 the seeded workload generators (no GPU code).  Run from the repository root:
 
-    python tests/golden/make_golden.py [sieve] [paper_files]
+    python tests/golden/make_golden.py [sieve] [paper_files] [region]
 
 Each output is JSON: {"config", "primes", "order", "ranges": [...], "results": [...]},
 one result per range: n_pairs, counts (caller order), survivors, roots.
@@ -42,7 +42,21 @@ def dump_paper_files(name, primes):
     print(f"{name}: {time.time() - t0:.1f} s")
 
 
+def dump_region(name, p_from, p_to, primes):
+    """Section 5 region scan of rows p_from..p_to (every q of Eq. 1.2) by the oracle."""
+    t0 = time.time()
+    T = O.Tables(primes, full_limit=0)
+    r = O.region_scan(T, p_from, p_to)
+    out = {"rows": [p_from, p_to], "primes": primes, "pairs": r["pairs"], "counts": r["counts"],
+           "survivors": r["survivors"], "roots": r["roots"], "depth": r["depth"], "r_max": r["r_max"]}
+    with open(os.path.join(HERE, name), "w") as f:
+        json.dump(out, f, separators=(",", ":"))
+    print(f"{name}: {time.time() - t0:.1f} s")
+
+
 def main(which):
+    if "region" in which:
+        dump_region("region_112600_112699.json", 112600, 112699, W.primes_between(11, 541))
     if "paper_files" in which:
         dump_paper_files("paper_files_11_541.json", W.primes_between(11, 541))
     if "sieve" not in which:
@@ -59,4 +73,4 @@ def main(which):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["sieve", "paper_files"])
+    main(sys.argv[1:] or ["sieve", "paper_files", "region"])

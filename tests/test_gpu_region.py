@@ -207,3 +207,20 @@ def test_theorem11_on_found_roots(cb, stream):
     flags = cb.cuboid_theorem11_flags(got["roots"])
     assert flags == [O.theorem_1_1_holds(*r) for r in got["roots"]] and not any(flags)
     assert got["cuboids"] == []
+
+
+def test_region_hundred_near_stop_example(cb, stream):
+    """The hundred of rows 112600..112699 (the hundred of the stop report printed in
+    section 5), every q of Eq. 1.2, primes 11..541 ascending: per-prime counts, pair
+    total and depth equal the oracle's stored scan (tests/golden/make_golden.py)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "region_112600_112699.json")))
+    t = _tables(cb, g["primes"], cb.ORDER_AS_GIVEN)
+    try:
+        st, rep, counts, surv, roots = cb.cuboid_region_scan(t, 112600, 112699, stream=stream)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert st == 0 and counts == g["counts"] and rep["pairs"] == g["pairs"]
+    assert sorted(surv) == [tuple(x) for x in g["survivors"]] and roots == []
+    assert (rep["depth"], rep["r_max"]) == (g["depth"], g["r_max"]) == (27, 127)
