@@ -214,11 +214,15 @@ def run_reference(args):
     for i in range(args.warmup):
         cpu_baseline(target_s=1.0, seed=W.DEFAULT_SEED + 1000 + i)
     per = min(10.0, max(2.0, 60.0 / max(args.steps, 1)))
+    wall = []
     for i in range(args.steps):
+        t0 = time.perf_counter()
         steps.append(cpu_baseline(target_s=per, seed=W.DEFAULT_SEED + i))
+        wall.append(time.perf_counter() - t0)
     v = sum(s["value"] for s in steps) / len(steps)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(wall) / len(wall),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": W.c2()["name"], "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": steps[-1]["sample"]},
