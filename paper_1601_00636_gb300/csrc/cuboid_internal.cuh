@@ -206,8 +206,12 @@ struct VerifyArgs {
   cuboid_root* roots;
   uint32_t* root_range;
   unsigned long long root_cap;
-  unsigned long long* zero_block = nullptr;  // cleared by block 0 after the sieve (may be null)
+  // cleared by block 0 after the sieve (may be null): the header and first pair total,
+  // and the first range's counts, of the result block the next single-range run uses
+  unsigned long long* zero_block = nullptr;
   uint32_t zero_words = 0;
+  unsigned long long* zero_block2 = nullptr;
+  uint32_t zero_words2 = 0;
 };
 
 // Launchers (each checks its own launch and returns cudaError_t).

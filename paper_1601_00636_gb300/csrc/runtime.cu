@@ -181,9 +181,12 @@ static VerifyArgs verify_args(cuboid_result* r, bool clear_other) {
   v.roots = r->d_roots;
   v.root_range = r->d_root_range;
   v.root_cap = r->root_cap;
-  if (clear_other) {
-    v.zero_block = reinterpret_cast<unsigned long long*>(r->d_blocks[r->cur ^ 1]);
-    v.zero_words = (uint32_t)(r->block_bytes / 8);
+  if (clear_other) {  // what a single-range run uses: header, pair total 0, counts of range 0
+    unsigned char* other = r->d_blocks[r->cur ^ 1];
+    v.zero_block = reinterpret_cast<unsigned long long*>(other);
+    v.zero_words = (uint32_t)((kHdrBytes + 8) / 8);
+    v.zero_block2 = reinterpret_cast<unsigned long long*>(other + kHdrBytes) + r->max_ranges;
+    v.zero_words2 = r->t->n;
   }
   return v;
 }
@@ -260,10 +263,11 @@ static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, c
     }
     return cudaGraphLaunch(g, s);
   }
-  if (n == 1 && r->max_ranges == 1) {
-    // One range on a one-range result: no plan kernel.  The run works in the block the
-    // last run did not use (cleared by that run's root test), every CTA plans the range
-    // itself, and this run's root test clears the other block for the next run.
+  if (n == 1) {
+    // One range: no plan kernel.  The run works in the block the last run did not use
+    // (whose header, first pair total and first counts that run's root test cleared, or
+    // which is still clear from the start), every CTA plans the range itself, and this
+    // run's root test clears the same parts of the other block for the next such run.
     use_block(r, r->cur ^ 1);
     SieveArgs sa = sieve_args(r, L, 0, 1);
     sa.self_plan = 1;

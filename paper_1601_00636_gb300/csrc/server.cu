@@ -138,7 +138,9 @@ static void dispatcher(cuboid_server* s) {
       }
       batch.clear();
       for (const Query& q : sl.queries) batch.push_back(q.range);
-      const int st = sieve_into(sl.res, batch.data(), (uint32_t)batch.size(), CUBOID_MODE_BATCHED, sl.stream,
+      // a lone query takes the single-range path (no plan kernel, no graph)
+      const uint32_t mode = batch.size() == 1 ? CUBOID_MODE_PLAIN : CUBOID_MODE_BATCHED;
+      const int st = sieve_into(sl.res, batch.data(), (uint32_t)batch.size(), mode, sl.stream,
                                 false, true);
       if (st != CUBOID_OK) {  // report the failure on every query of the batch
         std::lock_guard<std::mutex> lk(s->mu);

@@ -377,8 +377,10 @@ __device__ unsigned __int128 isqrt192(const U192& u) {
 
 __global__ void __launch_bounds__(64) k_verify(VerifyArgs a) {
   pdl_wait();  // the sieve grid's survivors and header are complete from here on
-  if (a.zero_block && blockIdx.x == 0)  // the other result block, for the next single-range run
+  if (a.zero_block && blockIdx.x == 0) {  // the other result block, for the next single-range run
     for (uint32_t i = threadIdx.x; i < a.zero_words; i += blockDim.x) a.zero_block[i] = 0ull;
+    for (uint32_t i = threadIdx.x; i < a.zero_words2; i += blockDim.x) a.zero_block2[i] = 0ull;
+  }
   ull n = a.hdr->n_surv;
   if (n > a.surv_cap) n = a.surv_cap;
   Ctx C;

@@ -593,3 +593,29 @@ def test_single_range_result_alternating_forms(cb, stream, c1_tables):
             _check_against([cb.cuboid_result_get(res, 0, 24)], [want[k]])
     finally:
         cb.cuboid_result_free(res)
+
+
+def test_multi_range_result_alternating_single_and_batched(cb, stream, c1_tables):
+    """A three-range result alternates single-range runs (plan-free, two blocks) with
+    batched and plain three-range runs; every run equals the oracle."""
+    rngs = [W.triangle(1200), W.rect(700, 900, 1, 3000), W.rect(5, 5, 1, 100000)]
+    want = O.run(W.first_odd_primes(24), rngs)["ranges"]
+    res = cb.cuboid_result_create(c1_tables, 3)
+    try:
+        seq = [[0], rngs, [1], [2], rngs, [0], "plain3", [1]]
+        for item in seq:
+            if item == "plain3":
+                cb.cuboid_sieve_into(res, rngs, cb.MODE_PLAIN, stream)
+                assert cb.cuboid_result_wait(res) == cb.OK
+                _check_against([cb.cuboid_result_get(res, i, 24) for i in range(3)], want)
+            elif item is rngs:
+                cb.cuboid_sieve_into(res, rngs, cb.MODE_BATCHED, stream)
+                assert cb.cuboid_result_wait(res) == cb.OK
+                _check_against([cb.cuboid_result_get(res, i, 24) for i in range(3)], want)
+            else:
+                k = item[0]
+                cb.cuboid_sieve_into(res, [rngs[k]], cb.MODE_PLAIN, stream)
+                assert cb.cuboid_result_wait(res) == cb.OK
+                _check_against([cb.cuboid_result_get(res, 0, 24)], [want[k]])
+    finally:
+        cb.cuboid_result_free(res)
