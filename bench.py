@@ -399,8 +399,8 @@ def run_ours(args):
                        "form": "plain (one range per launch)", "l2": "flushed (256 MiB write) before each step",
                        "parallelism": f"range shards x{world} (no data-path collective)"},
             "bit_exact": bit_exact, "table_build_ms": table_ms, "tuning": tune,
-            "roofline": roofline, "clocks": clk, "gpu_launches": 3 * args.steps,
-            "gpu_launches_note": "plan + sieve + root test per timed step (the sieve-timing pass adds as many)"}
+            "roofline": roofline, "clocks": clk, "gpu_launches": 2 * args.steps,
+            "gpu_launches_note": "sieve + root test per timed step (a single range needs no plan kernel); the sieve-timing pass adds as many"}
 
     if not args.no_extras and rank == 0:
         line["e2e"] = e2e_leg(cb, torch, primes, rng, args)
