@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         m *= inv;  // exact: pw divides m
         nfo += __popc(bal);
       }
-      if (m > 1) {  // a prime: above every trial prime tested, or below 9 if no batch ran
+      if (live && m > 1) {  // a prime: above every trial prime tested, or below 9 if no batch ran
         if (gl == 0) {
           const uint32_t mag = 0xFFFFFFFFu / m;
           s_fac[nfo] = make_uint4(m, mod_min(kStride, m, mag), m < 64 ? s_foff[m] : kBitTab,

@@ -619,3 +619,28 @@ def test_multi_range_result_alternating_single_and_batched(cb, stream, c1_tables
                 _check_against([cb.cuboid_result_get(res, 0, 24)], [want[k]])
     finally:
         cb.cuboid_result_free(res)
+
+
+@pytest.mark.parametrize("lanes", [8, 16])
+def test_grouped_rows_many_short_ranges(cb, stream, c1_tables, lanes):
+    """Thousands of one-row ranges with 8 or 16 lanes per row: the pair totals of every row
+    equal the oracle's, three times over (groups that idle at the end of a range must
+    leave no state behind for the rows their warp sieves next)."""
+    rows = [W.rect(x, x, 2, 3001, q_lt_p=True, allow_diagonal=True) for x in range(3, 3001)]
+    for i, r in enumerate(rows):
+        r["flags"] = (cb.ROWS_P, 0)[i % 2]
+    want = [len(O.row_pairs(r["p_lo"], r)) for r in rows]
+    t = cb.cuboid_tables_build(W.first_odd_primes(24), cb.ORDER_AS_GIVEN, stream)
+    try:
+        cb.cuboid_tables_set_tuning(t, row_lanes=lanes)
+        for _ in range(3):
+            res = cb.cuboid_result_create(t, len(rows))
+            try:
+                cb.cuboid_sieve_into(res, rows, cb.MODE_BATCHED, stream)
+                assert cb.cuboid_result_wait(res) == cb.OK
+                got = [cb.cuboid_result_get(res, i, 24)["n_pairs"] for i in range(len(rows))]
+            finally:
+                cb.cuboid_result_free(res)
+            assert got == want
+    finally:
+        cb.cuboid_tables_free(t)
