@@ -125,6 +125,23 @@ def peaks():
         return {}
 
 
+def profile_record(kernel_src: str, workload: str) -> dict:
+    """The committed ncu record of the sieve kernel for this workload (DRAM bytes, warp
+    instructions and issue-slot utilisation per launch), or {} when the kernel source
+    changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "sieve_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return {}
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    entry = rec.get(workload)
+    if not entry or entry.get("sieve_cu_sha256") != sha:
+        return {}
+    return entry
+
+
 def traffic_record(kernel_src: str, workload: str):
     """DRAM bytes per launch of the sieve kernel from a committed ncu summary, or None
     when the kernel source changed since the capture."""
@@ -383,8 +400,15 @@ def run_ours(args):
     achieved = alg_ops / (per_launch_ms / 1e3) / 1e12
     traffic = traffic_record(os.path.join(ROOT, "paper_1601_00636_gb300", "csrc", "sieve.cu"), cfg["name"])
     probe = int_issue_probe(cb, torch, stream)
+    prof = profile_record(os.path.join(ROOT, "paper_1601_00636_gb300", "csrc", "sieve.cu"), cfg["name"])
+    executed = None
+    if prof.get("inst_executed_per_launch"):
+        # every warp instruction the kernel issues, as lane-ops, over the live launch time
+        ex = prof["inst_executed_per_launch"] * 32 / (per_launch_ms / 1e3) / 1e12
+        executed = {"tops": ex, "frac": ex / alu_peak, "issue_active_pct_ncu": prof.get("issue_active_pct"),
+                    "note": "warp instructions per launch from the committed ncu record x 32 lanes / live launch time"}
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "traffic": traffic, "probe": probe,
+                "frac": achieved / alu_peak, "traffic": traffic, "probe": probe, "executed": executed,
                 "kernel": "k_sieve", "launch_ms": per_launch_ms,
                 "peak_note": f"{sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz (sm_max_mhz of measured)",
                 "work": {"word_steps": stats["word_steps"], "words": stats["words"],
