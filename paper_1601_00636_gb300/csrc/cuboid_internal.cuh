@@ -19,11 +19,13 @@ constexpr uint32_t kStageSpins = 1u << 22;    // polls of a CTA's staging barrie
 constexpr uint32_t kMaxChunkWords = 32768;   // 64-value words per subtile: at most 2^21 pairs
 constexpr uint32_t kMaxFactors = 10;       // distinct primes of a 32-bit integer <= 9
 
-// Coprimality mask image: for each odd prime f < 64 and offset t in [0, f) the 64-bit mask
-// of bits t, t + f, t + 2f, ... (as two uint32 halves), then the single bits 1 << t for t in
-// [0, 64) and an empty mask at index 64 (a factor f >= 64 hits a 64-value word at most
-// once); then, for each n < 64, the index of n's first mask if n is an odd prime, else the
-// single-bit block.  Built once with the tables; staged into each CTA's shared memory.
+// Coprimality mask image: for each odd prime f < 128 and offset t in [0, f) the 128-bit
+// mask of bits t, t + f, t + 2f, ... (as four uint32 quarters: two adjacent 64-value
+// words), then the single bits 1 << t for t in [0, 128) and an empty mask at index 128 (a
+// factor f >= 128 hits a pair of words at most once); then, for each n < 128, the index of
+// n's first mask if n is an odd prime, else the single-bit block.  Built once with the
+// tables; staged into each CTA's shared memory.
+constexpr uint32_t kPeriodicBelow = 128;  // factors below this get periodic masks
 constexpr uint32_t odd_prime_sum_below(uint32_t lim) {
   uint32_t s = 0;
   for (uint32_t f = 3; f < lim; f += 2) {
@@ -33,25 +35,25 @@ constexpr uint32_t odd_prime_sum_below(uint32_t lim) {
   }
   return s;
 }
-constexpr uint32_t kBitTab = odd_prime_sum_below(64);  // 499: masks of the odd primes below 64
-constexpr uint32_t kMaskTab = kBitTab + 65;            // 64-bit entries of the mask table
-static_assert(kBitTab == 499, "mask table layout");
-constexpr uint32_t kMaskImageWords = 2 * kMaskTab + 64;  // uint32 words: masks, then 64 offsets
+constexpr uint32_t kBitTab = odd_prime_sum_below(kPeriodicBelow);  // 1718: periodic masks
+constexpr uint32_t kMaskTab = kBitTab + 129;                       // 128-bit entries of the mask table
+static_assert(kBitTab == 1718, "mask table layout");
+constexpr uint32_t kMaskImageWords = 4 * kMaskTab + kPeriodicBelow;  // masks, then the offsets
 static_assert((kMaskImageWords * 4) % 16 == 0, "bulk-copy size");
-constexpr uint32_t kRowCacheLanes = 32;    // row offsets of the first 32 primes kept per lane
 
 // Per-prime sieve constants, one entry per prime in the effective order.  16 bytes.
 struct PrimeInfo {
   uint32_t r;      // the prime
   uint32_t magic;  // floor(2^32 / r): residue of a 32-bit n by one mul.hi and one fix-up
   uint32_t off;    // first word of row 0 in the window-row blob
-  uint32_t W;      // words per row: floor((r - 1) / 32) + 2
+  uint32_t W;      // words per row: floor((r - 1) / 32) + 5
 };
 
 // Window-row layout: row a of prime r holds W 32-bit words; bit j (0 <= j < 32 W) is
-// u_r(a, j mod r).  The 64 bits u_r(a, s), ..., u_r(a, s + 63 mod r) for any s < r are
-// two funnel shifts of words s/32, s/32 + 1 and s/32 + 2.
-__host__ __device__ inline uint32_t row_words(uint32_t r) { return (r - 1) / 32 + 3; }
+// u_r(a, j mod r).  The 128 bits u_r(a, s), ..., u_r(a, s + 127 mod r) for any s < r (two
+// adjacent 64-value words) are four funnel shifts of words s/32 ... s/32 + 4; the first
+// 64 of them are two funnel shifts of words s/32 ... s/32 + 2.
+__host__ __device__ inline uint32_t row_words(uint32_t r) { return (r - 1) / 32 + 5; }
 
 // One planned range.  32 bytes.
 struct TilePlan {
@@ -184,7 +186,7 @@ struct SieveArgs {
   uint32_t range_count;         // UINT32_MAX: read hdr->n_ranges
   uint32_t n_hot;               // hot primes (0, 2, 4, 5, 6 or 8): the first n_hot of the effective order
   uint32_t hot_r[8], hot_magic[8], hot_off[8], hot_W[8];
-  uint32_t hot_step[8];          // (64 row_lanes) mod r: a lane's stride between words
+  uint32_t hot_step[8];          // (128 row_lanes) mod r: a lane's stride between pairs of words
   uint32_t row_lanes;            // lanes per row (8, 16, 32)
   uint32_t stage_spins;          // polls of the staging barrier before a time-out
   // Single-range launch without a plan kernel (self_plan = 1): every CTA plans the range

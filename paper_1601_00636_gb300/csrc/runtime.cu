@@ -144,7 +144,7 @@ void fill_hot(SieveArgs& a, const cuboid_tables* t, const LaunchShape& L) {
     a.hot_magic[h] = pi.magic;
     a.hot_off[h] = pi.off;
     a.hot_W[h] = pi.W;
-    a.hot_step[h] = (64u * L.row_lanes) % pi.r;
+    a.hot_step[h] = (128u * L.row_lanes) % pi.r;  // a lane's stride between pairs of words
   }
 }
 

@@ -196,7 +196,7 @@ template <bool kSteps, int K, int kMaxThreads, int G>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   static_assert(G == 8 || G == 16 || G == 32, "lanes per row");
   constexpr uint32_t NG = 32 / G;                 // subtiles per tile (groups per warp)
-  constexpr uint32_t kStride = 64u * G;           // a lane's next word starts G words further on
+  constexpr uint32_t kStride = 128u * G;          // a lane's next pair of words starts 2 G words further on
   extern __shared__ uint4 smem_raw[];
   const uint32_t n = a.n_primes;
   const uint32_t warps = blockDim.x >> 5;
@@ -215,9 +215,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   TrialPrime* s_trial = reinterpret_cast<TrialPrime*>(s_info + n);                         // [kTrialSmem]
   uint4* s_fac_all = reinterpret_cast<uint4*>(s_trial + kTrialSmem);                       // [warps][NG][kMaxFactors]
   uint4* s_queue_all = s_fac_all + warps * NG * kMaxFactors;                               // [warps][kQueue]
-  uint2* s_mtab = reinterpret_cast<uint2*>(s_queue_all + warps * kQueue);                  // [kMaskTab]
-  uint32_t* s_foff = reinterpret_cast<uint32_t*>(s_mtab + kMaskTab);                       // [64]
-  uint32_t* s_fmag_all = s_foff + 64;                                                       // [warps][NG][kMaxFactors]
+  uint4* s_mtab = s_queue_all + warps * kQueue;                                             // [kMaskTab]
+  uint32_t* s_foff = reinterpret_cast<uint32_t*>(s_mtab + kMaskTab);                       // [kPeriodicBelow]
+  uint32_t* s_fmag_all = s_foff + kPeriodicBelow;                                                       // [warps][NG][kMaxFactors]
   uint32_t* s_cnt_all = s_fmag_all + warps * NG * kMaxFactors;                              // [warps][n]
   __shared__ __align__(8) unsigned long long s_bar;  // completion of the bulk copies
   __shared__ TilePlan s_self_plan;                    // the single range's plan (self_plan)
@@ -449,8 +449,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           }
           const uint32_t pos = nfo + __popc(bal & lanemask_lt);
           const uint32_t f = tp.f;
-          s_fac[pos] = make_uint4(f, mod_min(kStride, f, tp.lim), f < 64 ? s_foff[f] : kBitTab,
-                                  f < 64 ? f - 1 : 64u);
+          s_fac[pos] = make_uint4(f, mod_min(kStride, f, tp.lim), f < kPeriodicBelow ? s_foff[f] : kBitTab,
+                                  f < kPeriodicBelow ? f - 1 : 128u);
           s_fmag[pos] = tp.lim;  // floor(2^32 / f) for odd f > 1
         }
 #pragma unroll
@@ -464,22 +464,24 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
       if (live && m > 1) {  // a prime: above every trial prime tested, or below 9 if no batch ran
         if (gl == 0) {
           const uint32_t mag = 0xFFFFFFFFu / m;
-          s_fac[nfo] = make_uint4(m, mod_min(kStride, m, mag), m < 64 ? s_foff[m] : kBitTab,
-                                  m < 64 ? m - 1 : 64u);
+          s_fac[nfo] = make_uint4(m, mod_min(kStride, m, mag), m < kPeriodicBelow ? s_foff[m] : kBitTab,
+                                  m < kPeriodicBelow ? m - 1 : 128u);
           s_fmag[nfo] = mag;
         }
         ++nfo;
       }
-      // inert entries up to kFacRegs: offset 64 that never moves, empty mask
-      if (gl < (uint32_t)kFacRegs && gl >= nfo) s_fac[gl] = make_uint4(1u, 0u, kBitTab, 64u);
+      // inert entries up to kFacRegs: offset 128 that never moves, empty mask
+      if (gl < (uint32_t)kFacRegs && gl >= nfo) s_fac[gl] = make_uint4(1u, 0u, kBitTab, 128u);
       __syncwarp();
     }
-    // per-lane offset of the first multiple of each odd factor in the lane's first word
-    const uint32_t y0f = (wbeg + gl) << 6;
+    // Each lane sieves pairs of adjacent words (128 values): pair p of the subtile covers
+    // words wbeg + 2 p and wbeg + 2 p + 1, and lane gl takes the pairs gl, gl + G, ....
+    // Per-lane offset of the first multiple of each odd factor in the lane's first pair.
+    const uint32_t y0f = (wbeg + 2 * gl) << 6;
     uint32_t tf[kFacRegs];
 #pragma unroll
     for (int i = 0; i < kFacRegs; ++i) {
-      tf[i] = 64u;  // inert entry
+      tf[i] = 128u;  // inert entry
       if ((uint32_t)i < nfo) {
         const uint32_t f = s_fac[i].x;
         const uint32_t r = mod_min(y0f, f, s_fmag[i]);
@@ -497,11 +499,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     }
 
     const uint32_t emask = has2 ? 0xAAAAAAAAu : FULL;  // x even: y0 is even, so even y sit at even bits
-    const uint32_t nit = live ? (wend - wbeg) / G + 1 : 0u;  // words of this lane's group, per lane
+    const uint32_t npairs_sub = live ? (wend - wbeg) / 2 + 1 : 0u;  // pairs of words of the subtile
+    const uint32_t nit = (npairs_sub + G - 1) / G;                 // iterations of this lane's group
     const uint32_t maxit = G == 32 ? nit : __reduce_max_sync(FULL, nit);
-    // one word's alive mask: range edges, coprimality (odd factors; even y when x is
-    // even), diagonal; the factor offsets advance to the lane's next word
-    auto word_mask = [&](uint32_t w, bool on, uint32_t& al, uint32_t& ah) {
+    // one word's range edges and diagonal on top of its coprimality mask
+    auto finish_word = [&](uint32_t w, bool on, uint32_t ml, uint32_t mh, uint32_t& al, uint32_t& ah) {
       al = 0;
       ah = 0;
       if (on) {
@@ -509,24 +511,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         if (w == wlo) rm &= lo_mask;
         if (w == whi) rm &= hi_mask;
         const uint32_t rml = (uint32_t)rm, rmh = (uint32_t)(rm >> 32);
-        uint32_t ml = 0, mh = 0;  // union of the factor masks
-#pragma unroll
-        for (int i = 0; i < kFacRegs; ++i) {  // inert entries give an empty mask
-          const uint4 fc = s_fac[i];          // {f, (64 G) mod f, table base, cap}
-          const uint2 mk = s_mtab[fc.z + min(tf[i], fc.w)];
-          ml |= mk.x;
-          mh |= mk.y;
-          // the lane's next word starts 64 G further on: t <- (t - 64 G) mod f
-          tf[i] = tf[i] >= fc.y ? tf[i] - fc.y : tf[i] - fc.y + fc.x;
-        }
-        for (uint32_t i = kFacRegs; i < nfo; ++i) {
-          const uint4 fc = s_fac[i];
-          const uint32_t s = mod_min(w << 6, fc.x, s_fmag[i]);
-          const uint32_t t = s ? fc.x - s : 0u;
-          const uint2 mk = s_mtab[fc.z + min(t, fc.w)];
-          ml |= mk.x;
-          mh |= mk.y;
-        }
         al = rml & emask & ~ml;
         ah = rmh & emask & ~mh;
         if (w == dword) {
@@ -553,34 +537,54 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
                       false);
       }
     };
-    // two words a lane per iteration (G words apart), whose hot-prime chains interleave
-    uint32_t wb = wbeg;
-    for (uint32_t j = 0; j < maxit; j += 2, wb += 2 * G) {
-      const uint32_t wA = wb + gl, wB = wA + G;
+    uint32_t wb = wbeg + 2 * gl;
+    for (uint32_t j = 0; j < maxit; ++j, wb += 2 * G) {
+      const uint32_t wA = wb, wB = wb + 1;  // the lane's pair of adjacent words
+      const bool onA = j < nit && wA <= wend, onB = j < nit && wB <= wend;
+      // coprimality masks of both words at once: 128-bit masks from the image
+      uint4 m = make_uint4(0u, 0u, 0u, 0u);
+      if (onA) {
+#pragma unroll
+        for (int i = 0; i < kFacRegs; ++i) {  // inert entries give an empty mask
+          const uint4 fc = s_fac[i];          // {f, (128 G) mod f, table base, cap}
+          const uint4 mk = s_mtab[fc.z + min(tf[i], fc.w)];
+          m.x |= mk.x;
+          m.y |= mk.y;
+          m.z |= mk.z;
+          m.w |= mk.w;
+          // the lane's next pair starts 128 G further on: t <- (t - 128 G) mod f
+          tf[i] = tf[i] >= fc.y ? tf[i] - fc.y : tf[i] - fc.y + fc.x;
+        }
+        for (uint32_t i = kFacRegs; i < nfo; ++i) {
+          const uint4 fc = s_fac[i];
+          const uint32_t s = mod_min(wA << 6, fc.x, s_fmag[i]);
+          const uint32_t t = s ? fc.x - s : 0u;
+          const uint4 mk = s_mtab[fc.z + min(t, fc.w)];
+          m.x |= mk.x;
+          m.y |= mk.y;
+          m.z |= mk.z;
+          m.w |= mk.w;
+        }
+      }
       uint32_t alA, ahA, alB, ahB;
-      word_mask(wA, j < nit && wA <= wend, alA, ahA);
-      word_mask(wB, j + 1 < nit && wB <= wend, alB, ahB);
-      // hot primes: no early-exit test
+      finish_word(wA, onA, m.x, m.y, alA, ahA);
+      finish_word(wB, onB, m.z, m.w, alB, ahB);
+      // hot primes: no early-exit test; one 128-bit window serves both words
 #pragma unroll
       for (int h = 0; h < K; ++h) {
         if (kSteps) st_wsteps += ((alA | ahA) ? 1 : 0) + ((alB | ahB) ? 1 : 0);
-        const uint32_t r = a.hot_r[h], step = a.hot_step[h];  // step = (64 G) mod r
-        const uint32_t sA = sh[h];
-        const uint32_t t1 = sA + step;
-        const uint32_t sB = min(t1, t1 - r);
-        const uint32_t t2 = sB + step;
-        sh[h] = min(t2, t2 - r);
-        const uint32_t* pA = s_tab + rb[h] + (sA >> 5);
-        const uint32_t* pB = s_tab + rb[h] + (sB >> 5);
-        const uint32_t a0 = pA[0], a1 = pA[1], a2 = pA[2];
-        const uint32_t b0 = pB[0], b1 = pB[1], b2 = pB[2];
-        alA &= ~__funnelshift_r(a0, a1, sA);  // the window of u_r(x mod r, y0 mod r ...)
-        ahA &= ~__funnelshift_r(a1, a2, sA);
-        alB &= ~__funnelshift_r(b0, b1, sB);
-        ahB &= ~__funnelshift_r(b1, b2, sB);
+        const uint32_t s = sh[h];
+        const uint32_t sn = s + a.hot_step[h];  // next pair: + (128 G) mod r, below 2r
+        sh[h] = min(sn, sn - a.hot_r[h]);
+        const uint32_t* tp = s_tab + rb[h] + (s >> 5);
+        const uint32_t w0 = tp[0], w1 = tp[1], w2 = tp[2], w3 = tp[3], w4 = tp[4];
+        alA &= ~__funnelshift_r(w0, w1, s);  // the window of u_r(x mod r, y0 mod r ...)
+        ahA &= ~__funnelshift_r(w1, w2, s);
+        alB &= ~__funnelshift_r(w2, w3, s);
+        ahB &= ~__funnelshift_r(w3, w4, s);
         hs[h] += __popc(alA) + __popc(ahA) + __popc(alB) + __popc(ahB);
       }
-      if (kSteps) st_warpsteps += (j + 1 < maxit) ? 2 * K : K;
+      if (kSteps) st_warpsteps += 2 * K;
       enqueue(alA, ahA, wA << 6);
       enqueue(alB, ahB, wB << 6);
     }
@@ -670,7 +674,7 @@ size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads
   return (((size_t)smem_words * 4 + 15) & ~(size_t)15) + (size_t)n_primes * sizeof(PrimeInfo) +
          (size_t)kTrialSmem * sizeof(TrialPrime) +
          (size_t)warps * groups * kMaxFactors * sizeof(uint4) +
-         (size_t)warps * kQueue * sizeof(uint4) + kMaskTab * sizeof(uint2) + 64 * sizeof(uint32_t) +
+         (size_t)warps * kQueue * sizeof(uint4) + kMaskTab * sizeof(uint4) + kPeriodicBelow * sizeof(uint32_t) +
          (size_t)warps * groups * kMaxFactors * sizeof(uint32_t) +
          (size_t)warps * n_primes * sizeof(uint32_t);
 }

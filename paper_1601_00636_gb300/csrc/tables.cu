@@ -372,24 +372,16 @@ int build_tables(const uint32_t* primes, uint32_t n, uint32_t flags, cudaStream_
     if (img.empty()) {
       img.assign(kMaskImageWords, 0);
       uint32_t base = 0;
-      for (uint32_t f = 3; f < 64; f += 2) {
+      for (uint32_t f = 3; f < kPeriodicBelow; f += 2) {
         if (!is_prime_host(f)) continue;
-        for (uint32_t t = 0; t < f; ++t) {
-          unsigned long long m = 0;
-          for (uint32_t b = t; b < 64; b += f) m |= 1ull << b;
-          img[2 * (base + t)] = (uint32_t)m;
-          img[2 * (base + t) + 1] = (uint32_t)(m >> 32);
-        }
-        img[2 * kMaskTab + f] = base;
+        for (uint32_t t = 0; t < f; ++t)
+          for (uint32_t b = t; b < 128; b += f) img[4 * (base + t) + b / 32] |= 1u << (b % 32);
+        img[4 * kMaskTab + f] = base;
         base += f;
       }
-      for (uint32_t b = 0; b < 64; ++b) {
-        const unsigned long long m = 1ull << b;
-        img[2 * (kBitTab + b)] = (uint32_t)m;
-        img[2 * (kBitTab + b) + 1] = (uint32_t)(m >> 32);
-      }
-      for (uint32_t n2 = 0; n2 < 64; ++n2)
-        if (n2 < 3 || n2 % 2 == 0 || !is_prime_host(n2)) img[2 * kMaskTab + n2] = kBitTab;
+      for (uint32_t b = 0; b < 128; ++b) img[4 * (kBitTab + b) + b / 32] = 1u << (b % 32);
+      for (uint32_t n2 = 0; n2 < kPeriodicBelow; ++n2)
+        if (n2 < 3 || n2 % 2 == 0 || !is_prime_host(n2)) img[4 * kMaskTab + n2] = kBitTab;
     }
     CK(cudaMalloc(&t->d_mimg, kMaskImageWords * sizeof(uint32_t)));
     CK(cudaMemcpyAsync(t->d_mimg, img.data(), kMaskImageWords * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
