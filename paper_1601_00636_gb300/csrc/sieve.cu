@@ -1,21 +1,22 @@
 // K2 + K3: the bit sieve of section 2 / the search loop of section 5, on the device.
 //
-// Work unit ("tile"): one row value x (p, or q when the rectangle is narrow in q) and a
-// chunk of consecutive 64-value words of the other coordinate y.  Each lane owns one
-// 64-bit word of y values (y0 = 64 w .. 64 w + 63) and carries an "alive" mask of the
-// pairs still in play:
+// Work unit ("subtile"): one row value x (p, or q when the rectangle is narrow in q) and
+// a chunk of consecutive 64-value words of the other coordinate y; a warp takes 32 / G
+// subtiles at a time (G lanes per row).  Each lane sieves two adjacent 64-bit words of y
+// values at a time (y0 = 64 w .. 64 w + 127) and carries an "alive" mask of the pairs
+// still in play:
 //   alive = in-range bits & ~(bits of y sharing a prime factor with x) & ~diagonal,
 // then for each prime of the effective order
 //   rej   = window(u_r row x mod r, starting at y0 mod r) & alive
 //   count[prime] += popc(rej);  alive &= ~rej
-// The window is two funnel shifts of three 32-bit words of the window-row table (see
-// cuboid_internal.cuh).  The first K primes ("hot") are applied to every word without an
-// early-exit test, with their moduli in the constant bank and their counts in registers;
-// words still alive afterwards go to a per-warp queue and are finished 32 at a time
-// with a warp-uniform early exit.  Survivors (alive bits after the last prime) are
-// compacted with a warp prefix sum and one atomic per warp.  Tiles come from a device
-// queue (one atomic per tile), so one kernel serves one range per launch and thousands
-// of ranges per launch.
+// The 128-bit window of a pair of words is four funnel shifts of five 32-bit words of
+// the window-row table (see cuboid_internal.cuh).  The first K primes ("hot") are applied
+// to every word without an early-exit test, with their moduli in the constant bank and
+// their counts kept as per-lane sums; words still alive afterwards go to a per-warp queue
+// and are finished 32 at a time with a warp-uniform early exit.  Survivors (alive bits
+// after the last prime) are compacted with a warp prefix sum and one atomic per warp.
+// Tiles come from a device queue (one atomic per tile), so one kernel serves one range
+// per launch and thousands of ranges per launch.
 #include <mutex>
 
 #include "cuboid_internal.cuh"
@@ -189,7 +190,7 @@ __device__ __forceinline__ void drain(const SieveArgs& a, const PrimeInfo* s_inf
 // 512 lets a single 512-thread CTA per SM use up to 128 registers.
 // G: lanes per row.  A warp takes one tile = 32 / G consecutive subtiles of a range (a
 // subtile is one row and one chunk of its 64-value words); each group of G lanes sieves
-// one subtile, its lanes on words G apart.  G = 32 is one subtile per warp; smaller groups
+// one subtile, each lane a pair of adjacent words at a time, lanes on pairs G apart.  G = 32 is one subtile per warp; smaller groups
 // share the per-row setup (factors of the row value, residues of the hot primes) among
 // fewer words, which pays on short rows.
 template <bool kSteps, int K, int kMaxThreads, int G>
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
 
     // ---- distinct odd prime factors of x (trial division shared by the group's lanes)
     // Each lane tests one trial prime per batch; a lane that divides x writes its factor
-    // entry {f, (64 G) mod f, mask table base, cap} and its reciprocal, and divides its
+    // entry {f, (128 G) mod f, mask table base, cap} and its reciprocal, and divides its
     // prime power out of the cofactor through a product over the group.
     uint32_t nfo = 0;  // uniform in the group
     bool has2 = false;
