@@ -431,6 +431,7 @@ def run_ours(args):
         line["forms"] = forms_leg(cb, torch, stream, flush)
         line["serving"] = serving_leg(cb, torch, stream)
         line["region_section6"] = region_leg(cb, torch, stream)
+        line["wide_64bit"] = wide_leg(cb, torch, stream)
         line["cpu_baseline"] = cpu_baseline()
     elif rank == 0:
         line["e2e"] = None
@@ -632,6 +633,40 @@ def region_leg(cb, torch, stream, p_to=154000):
             "wall_s": wall, "pairs_per_s": rep["pairs"] / wall, "n_surv": rep["n_surv"],
             "depth": rep["depth"], "r_max": rep["r_max"],
             "paper": "4130 min on its machine for the same rows (section 6; context only)"}
+
+
+def wide_leg(cb, torch, stream, rows=16):
+    """64-bit ranges: the rows p = p_max + 1 .. p_max + 16 just beyond the 32-bit limit of
+    section 6 (p_max = 72796055), every q of Eq. 1.2 (q up to 59 p > 2^32: each row is a
+    32-bit piece and a based piece), the 96 primes 11..541 ascending, through
+    cuboid_sieve_wide; beside it the 16 rows just below p_max (32-bit pieces only) through
+    the same call.  Device time (CUDA events around the enqueue, copies back included) and
+    pairs/s; each row's counts and survivors must add up to its pair total."""
+    p_max = 72796055
+    primes = W.primes_between(11, 541)
+    t = cb.cuboid_tables_build(primes, cb.ORDER_AS_GIVEN, stream)
+    out = {}
+    for name, p0 in (("beyond_p_max", p_max + 1), ("below_p_max", p_max - rows + 1)):
+        rngs = [W.rect(p, p, cb.cuboid_region_qmin(p), 59 * p) for p in range(p0, p0 + rows)]
+        for it in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                res = cb.cuboid_sieve_wide(t, rngs, stream=stream)
+                b.record(stream)
+            st = cb.cuboid_result_wait(res)
+            ms = a.elapsed_time(b)
+            got = [cb.cuboid_result_get_wide(res, i, len(primes)) for i in range(rows)]
+            cb.cuboid_result_free(res)
+        pairs = sum(g["n_pairs"] for g in got)
+        out[name] = {"rows": [p0, p0 + rows - 1], "q": "q_lo(p) .. 59 p (Eq. 1.2)", "status": st,
+                     "pieces": sum(len(cb.cuboid_wide_pieces(r)) for r in rngs), "pairs": pairs, "ms": ms,
+                     "pairs_per_s": pairs / (ms / 1e3), "n_surv": sum(len(g["survivors"]) for g in got),
+                     "q_max": 59 * (p0 + rows - 1),
+                     "sums_ok": all(sum(g["counts"]) + len(g["survivors"]) == g["n_pairs"] for g in got)}
+    cb.cuboid_tables_free(t)
+    out["primes"] = "11..541 (96, ascending)"
+    return out
 
 
 def main():

@@ -20,7 +20,8 @@
  *   - Objects are bound to the CUDA device that was current when they were created;
  *     use them with that device current.  The library owns every device and pinned
  *     host buffer it allocates; handles are freed by the matching *_free/_destroy.
- *   - Ranges are inclusive on both ends; p and q are 32-bit (1 <= p, q <= 2^32 - 1).
+ *   - Ranges are inclusive on both ends; p and q are 32-bit (1 <= p, q <= 2^32 - 1),
+ *     except in the calls of the "64-bit ranges" section (p, q < 2^40).
  *   - Counts are indexed by the caller's prime list.  counts[i] is the number of pairs
  *     whose FIRST rejecting prime, in the effective order, is primes[i].
  */
@@ -389,6 +390,73 @@ int cuboid_shard_range(const cuboid_range* r, uint32_t k, uint32_t i, cuboid_ran
  * *n_roots their number.  Synchronous on stream.  Errors: EINVAL, EOVERFLOW, EVERIFY. */
 int cuboid_verify_pairs(const uint32_t* p, const uint32_t* q, uint32_t n, void* stream,
                         cuboid_root* roots_out, uint64_t cap, uint64_t* n_roots);
+
+/* ================================================================ 64-bit ranges */
+
+/* Section 6 puts the limit of the paper's 32-bit code at p_max = 2^32 / 59 (72796055):
+ * beyond it the top of the region of Eq. 1.2, q = 59 p, leaves 32 bits.  The calls below
+ * take p and q as 64-bit integers below CUBOID_WIDE_LIMIT = 2^40, which holds the region
+ * of Eq. 1.2 for every p < 2^32 (59 p < 2^38).  One coordinate, the one whose values index
+ * the rows of the sieve's tiles, must stay below 2^32 (coprimality with the other
+ * coordinate is decided from its factorisation): rows of p when p_hi < 2^32, else rows of
+ * q when q_hi < 2^32 (CUBOID_ROWS_P / CUBOID_ROWS_Q force one; with neither flag and both
+ * below 2^32 the range is a 32-bit range, oriented as in cuboid_sieve).  The other
+ * coordinate ("y") is cut into pieces: the values below 2^32 form one piece, sieved as a
+ * 32-bit range; above 2^32 each piece holds at most 2^32 - 64 values and is sieved
+ * relative to a 64-bit base (a multiple of 64), whose residues modulo the table primes and
+ * the row's prime factors offset those of the relative values.  A piece above 2^32 lies
+ * above every row value, so a CUBOID_Q_LT_P range keeps all of it (rows of q) or none of it
+ * (rows of p), and it holds no diagonal pair.  Results are per range, as for 32-bit
+ * ranges. */
+#define CUBOID_WIDE_LIMIT (1ull << 40)
+
+/* A 64-bit rectangle; flags as for cuboid_range; reserved must be 0.  40 bytes. */
+typedef struct cuboid_range_wide {
+  uint64_t p_lo, p_hi, q_lo, q_hi;
+  uint32_t flags;
+  uint32_t reserved;
+} cuboid_range_wide;
+
+/* An integer root t > 0 of Q_pq with 64-bit p, q (t = t_hi * 2^64 + t_lo). */
+typedef struct cuboid_root_wide {
+  uint64_t p, q;
+  uint64_t t_lo, t_hi;
+} cuboid_root_wide;
+
+/* The pieces of one wide range, as sieved: pieces[i] holds the piece in coordinates
+ * relative to bases[2 i] (added to p) and bases[2 i + 1] (added to q), with CUBOID_ROWS_P
+ * or CUBOID_ROWS_Q set; a piece that the CUBOID_Q_LT_P restriction leaves empty is not
+ * listed.  cap is the capacity of pieces (and of bases, in pairs); *n gets the number of
+ * pieces even when it exceeds cap (then EOVERFLOW and nothing else is written).  Host
+ * only, no CUDA call.  Errors: EINVAL (NULL, bad flags or reserved), ERANGE (a bound 0
+ * or >= 2^40, lo > hi, or no coordinate below 2^32 to index the rows), EOVERFLOW. */
+int cuboid_wide_pieces(const cuboid_range_wide* r, cuboid_range* pieces, uint64_t* bases, uint32_t cap,
+                       uint32_t* n);
+
+/* Sieve n wide ranges (host array): for each piece one plan and one sieve launch, then one
+ * root test for all survivors, enqueued on stream with the copies back; creates *out
+ * (default record capacities).  Wait with cuboid_result_wait and read with
+ * cuboid_result_get_wide (cuboid_result_get refuses such a result: its internal ranges are
+ * the pieces).  Errors: ENOTABLES, EINVAL, ERANGE (as cuboid_wide_pieces), ENOMEM. */
+int cuboid_sieve_wide(const cuboid_tables* t, const cuboid_range_wide* ranges, uint32_t n, void* stream,
+                      cuboid_result** out);
+
+/* Results of wide range range_idx (valid after cuboid_result_wait): n_pairs and counts as
+ * for cuboid_result_get; surv: 2 n_surv values p0, q0, p1, q1, ... ascending by (p, q);
+ * roots ascending by (p, q, t).  Arrays are owned by res; any output may be NULL.
+ * Errors: EINVAL (not waited for, not a wide result, range_idx out of range). */
+int cuboid_result_get_wide(const cuboid_result* res, uint32_t range_idx, uint64_t* n_pairs,
+                           uint64_t* counts, uint64_t* n_surv, const uint64_t** surv, uint64_t* n_roots,
+                           const cuboid_root_wide** roots);
+
+/* The exact integer-root test on n arbitrary 64-bit pairs (host arrays, 1 <= p, q < 2^40),
+ * as cuboid_verify_pairs.  Errors: EINVAL, ERANGE, EOVERFLOW, EVERIFY. */
+int cuboid_verify_pairs_wide(const uint64_t* p, const uint64_t* q, uint32_t n, void* stream,
+                             cuboid_root_wide* roots_out, uint64_t cap, uint64_t* n_roots);
+
+/* Theorem 1.1 flags for wide roots (p, q < 2^40), as cuboid_theorem11_flags.
+ * Errors: EINVAL, ERANGE. */
+int cuboid_theorem11_flags_wide(const cuboid_root_wide* roots, uint64_t n, uint8_t* flags);
 
 /* ================================================================ serving */
 

@@ -474,6 +474,16 @@ def region_pair_count(p_from: int, p_to: int) -> int:
     return total
 
 
+def coprime_count(p: int, q_lo: int, q_hi: int) -> int:
+    """Number of q in [q_lo, q_hi] with gcd(p, q) = 1 (the pairs of row p that are sieved,
+    before the p != q rule), by Moebius inversion over the squarefree divisors d of p:
+    sum_{d | p} mu(d) (floor(q_hi / d) - floor((q_lo - 1) / d)).  Any size of q."""
+    divs = [(1, 1)]
+    for f in _factor(p):
+        divs += [(d * f, -s) for (d, s) in divs]
+    return sum(s * (q_hi // d - (q_lo - 1) // d) for (d, s) in divs) if q_hi >= q_lo else 0
+
+
 # --------------------------------------------------------------------------------------
 # The paper's table files (section 2, section 3)
 # --------------------------------------------------------------------------------------

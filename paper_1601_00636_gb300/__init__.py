@@ -59,6 +59,15 @@ class cuboid_root(C.Structure):
     _fields_ = [("p", C.c_uint32), ("q", C.c_uint32), ("t_lo", C.c_uint64), ("t_hi", C.c_uint64)]
 
 
+class cuboid_range_wide(C.Structure):
+    _fields_ = [("p_lo", C.c_uint64), ("p_hi", C.c_uint64), ("q_lo", C.c_uint64),
+                ("q_hi", C.c_uint64), ("flags", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class cuboid_root_wide(C.Structure):
+    _fields_ = [("p", C.c_uint64), ("q", C.c_uint64), ("t_lo", C.c_uint64), ("t_hi", C.c_uint64)]
+
+
 class cuboid_tuning(C.Structure):
     _fields_ = [("block_threads", C.c_uint32), ("ctas_per_sm", C.c_uint32),
                 ("smem_primes", C.c_uint32), ("tiles_per_warp", C.c_uint32),
@@ -116,6 +125,15 @@ _SIGS = {
                                      C.POINTER(_u64)]),
     "cuboid_verify_pairs": (C.c_int, [C.POINTER(_u32), C.POINTER(_u32), _u32, _P, C.POINTER(cuboid_root),
                                       _u64, C.POINTER(_u64)]),
+    "cuboid_wide_pieces": (C.c_int, [C.POINTER(cuboid_range_wide), C.POINTER(cuboid_range), C.POINTER(_u64), _u32,
+                                     C.POINTER(_u32)]),
+    "cuboid_sieve_wide": (C.c_int, [_P, C.POINTER(cuboid_range_wide), _u32, _P, C.POINTER(_P)]),
+    "cuboid_result_get_wide": (C.c_int, [_P, _u32, C.POINTER(_u64), C.POINTER(_u64), C.POINTER(_u64),
+                                         C.POINTER(C.POINTER(_u64)), C.POINTER(_u64),
+                                         C.POINTER(C.POINTER(cuboid_root_wide))]),
+    "cuboid_verify_pairs_wide": (C.c_int, [C.POINTER(_u64), C.POINTER(_u64), _u32, _P,
+                                           C.POINTER(cuboid_root_wide), _u64, C.POINTER(_u64)]),
+    "cuboid_theorem11_flags_wide": (C.c_int, [C.POINTER(cuboid_root_wide), _u64, C.POINTER(C.c_uint8)]),
     "cuboid_server_create": (C.c_int, [_P, _u64, _u32, C.POINTER(_P)]),
     "cuboid_server_submit": (C.c_int, [_P, C.POINTER(cuboid_range), C.POINTER(_u64)]),
     "cuboid_server_poll": (C.c_int, [_P, _u64, C.POINTER(_P)]),
@@ -449,6 +467,77 @@ def cuboid_verify_pairs(ps, qs, stream=None, cap: int | None = None):
     nr = _u64()
     _check(_lib.cuboid_verify_pairs(pa, qa, n, _stream(stream), out, cap, C.byref(nr)), "cuboid_verify_pairs")
     return [(out[i].p, out[i].q, (int(out[i].t_hi) << 64) | int(out[i].t_lo)) for i in range(nr.value)]
+
+
+# ------------------------------------------------------------------ 64-bit ranges
+
+WIDE_LIMIT = 1 << 40
+
+
+def wide_range(d: dict) -> cuboid_range_wide:
+    """A cuboid_range_wide from a range dict (p_lo, p_hi, q_lo, q_hi, q_lt_p,
+    allow_diagonal, flags)."""
+    fl = (Q_LT_P if d.get("q_lt_p") else 0) | (ALLOW_DIAGONAL if d.get("allow_diagonal") else 0) | d.get("flags", 0)
+    return cuboid_range_wide(d["p_lo"], d["p_hi"], d["q_lo"], d["q_hi"], fl, d.get("reserved", 0))
+
+
+def cuboid_wide_pieces(rng: dict):
+    """The pieces of a 64-bit range: [(piece dict with relative bounds and flags, p base, q base)]."""
+    r = wide_range(rng)
+    n = _u32()
+    st = _lib.cuboid_wide_pieces(C.byref(r), None, None, 0, C.byref(n))
+    if st not in (OK, EOVERFLOW):
+        _check(st, "cuboid_wide_pieces")
+    cap = max(n.value, 1)
+    pcs = (cuboid_range * cap)()
+    bases = (_u64 * (2 * cap))()
+    _check(_lib.cuboid_wide_pieces(C.byref(r), pcs, bases, cap, C.byref(n)), "cuboid_wide_pieces")
+    return [({"p_lo": pcs[i].p_lo, "p_hi": pcs[i].p_hi, "q_lo": pcs[i].q_lo, "q_hi": pcs[i].q_hi,
+              "flags": pcs[i].flags}, int(bases[2 * i]), int(bases[2 * i + 1])) for i in range(n.value)]
+
+
+def cuboid_sieve_wide(t, ranges, stream=None) -> int:
+    """Sieve 64-bit ranges (dicts); returns the result handle (wait, then cuboid_result_get_wide)."""
+    arr = (cuboid_range_wide * len(ranges))(*[wide_range(d) for d in ranges])
+    out = _P()
+    _check(_lib.cuboid_sieve_wide(t, arr, len(ranges), _stream(stream), C.byref(out)), "cuboid_sieve_wide")
+    return out.value
+
+
+def cuboid_result_get_wide(res, range_idx: int, n_primes: int) -> dict:
+    npairs, ns, nr = _u64(), _u64(), _u64()
+    counts = (_u64 * n_primes)()
+    sp, rp = C.POINTER(_u64)(), C.POINTER(cuboid_root_wide)()
+    _check(_lib.cuboid_result_get_wide(res, range_idx, C.byref(npairs), counts, C.byref(ns), C.byref(sp),
+                                       C.byref(nr), C.byref(rp)), "cuboid_result_get_wide")
+    surv = [(int(sp[2 * i]), int(sp[2 * i + 1])) for i in range(ns.value)]
+    roots = [(int(rp[i].p), int(rp[i].q), (int(rp[i].t_hi) << 64) | int(rp[i].t_lo)) for i in range(nr.value)]
+    cuboids = [rt for rt, f in zip(roots, cuboid_theorem11_flags_wide(roots)) if f] if roots else []
+    return {"n_pairs": npairs.value, "counts": counts[:], "survivors": surv, "roots": roots,
+            "cuboids": cuboids}
+
+
+def cuboid_verify_pairs_wide(ps, qs, stream=None, cap: int | None = None):
+    n = len(ps)
+    pa = (_u64 * max(n, 1))(*ps)
+    qa = (_u64 * max(n, 1))(*qs)
+    cap = cap if cap is not None else 5 * n + 5
+    out = (cuboid_root_wide * cap)()
+    nr = _u64()
+    _check(_lib.cuboid_verify_pairs_wide(pa, qa, n, _stream(stream), out, cap, C.byref(nr)),
+           "cuboid_verify_pairs_wide")
+    return [(int(out[i].p), int(out[i].q), (int(out[i].t_hi) << 64) | int(out[i].t_lo)) for i in range(nr.value)]
+
+
+def cuboid_theorem11_flags_wide(roots) -> list[bool]:
+    """Theorem 1.1 on (p, q, t) roots with p, q < 2^40."""
+    n = len(roots)
+    arr = (cuboid_root_wide * max(n, 1))()
+    for i, (p, q, t) in enumerate(roots):
+        arr[i] = cuboid_root_wide(p, q, t & ((1 << 64) - 1), t >> 64)
+    out = (C.c_uint8 * max(n, 1))()
+    _check(_lib.cuboid_theorem11_flags_wide(arr, n, out), "cuboid_theorem11_flags_wide")
+    return [bool(out[i]) for i in range(n)]
 
 
 # ------------------------------------------------------------------ serving

@@ -197,6 +197,11 @@ struct SieveArgs {
   const cuboid_range* self_range = nullptr;
   cuboid_range self_range_val = {};
   uint32_t n_sms;               // SMs of the device (picks the register budget of the variant)
+  // Piece of a 64-bit range: the planned y (word) coordinates are relative to y_base, a
+  // multiple of 64 at or above 2^32 - 64, and every y of the piece is at least 2^32, above
+  // any 32-bit row value x (so the piece holds no diagonal pair and no triangle edge).
+  // 0: a 32-bit range.
+  unsigned long long y_base = 0;
 };
 constexpr uint32_t kMaxHot = 8;
 
@@ -208,6 +213,9 @@ struct VerifyArgs {
   cuboid_root* roots;
   uint32_t* root_range;
   unsigned long long root_cap;
+  // 64-bit ranges (may be null): per range index k, base[2 k] and base[2 k + 1] are added
+  // to the record's p and q (the sieve writes them relative to the piece's base)
+  const unsigned long long* base = nullptr;
   // cleared by block 0 after the sieve (may be null): the header and first pair total,
   // and the first range's counts, of the result block the next single-range run uses
   unsigned long long* zero_block = nullptr;
@@ -228,7 +236,8 @@ cudaError_t launch_reset(DevHeader* hdr, uint32_t n_ranges, cudaStream_t s);
 // reads what that kernel wrote).  Only when the previous stream operation is that kernel.
 cudaError_t launch_sieve(const SieveArgs& a, bool count_steps, uint32_t blocks,
                          uint32_t threads, size_t smem, cudaStream_t s, bool pdl = false);
-size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads, uint32_t row_lanes);
+size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads, uint32_t row_lanes,
+                        bool wide = false);
 cudaError_t sieve_set_smem_limit(bool count_steps, size_t bytes);
 cudaError_t launch_verify(const VerifyArgs& a, uint32_t blocks, cudaStream_t s, bool pdl = false);
 
@@ -262,8 +271,9 @@ struct LaunchShape {
   size_t smem;
 };
 void fill_hot(SieveArgs& a, const cuboid_tables* t, const LaunchShape& L);
-// count_steps: the step-counting build, which exists for whole-warp rows only.
-LaunchShape launch_shape(const cuboid_tables* t, bool count_steps = false);
+// count_steps: the step-counting build, which exists for whole-warp rows only.  wide: the
+// build for pieces of 64-bit ranges (whole-warp rows, more shared memory).
+LaunchShape launch_shape(const cuboid_tables* t, bool count_steps = false, bool wide = false);
 
 // packed: NULL (tables from the definition), or per caller index the host address of the
 // prime's Eq. 2.6 bytes (ceil(r^2 / 8)), which become the full tables as they are.

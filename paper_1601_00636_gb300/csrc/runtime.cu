@@ -71,6 +71,17 @@ struct cuboid_result {
   uint32_t timed_launches = 0;
   float sieve_ms = 0.f;
   bool host_only = false;        // results delivered by the server (no device buffers)
+  // 64-bit ranges: the run's ranges are the pieces; piece k belongs to range piece_of[k]
+  // and its records are relative to h_base[2 k] (p) and h_base[2 k + 1] (q)
+  bool wide = false;
+  uint32_t n_wide = 0;
+  std::vector<uint32_t> piece_of;
+  std::vector<unsigned long long> h_base;
+  unsigned long long* d_base = nullptr;
+  size_t d_base_cap = 0;
+  std::vector<uint64_t> wcounts, wnpairs;
+  std::vector<std::vector<uint64_t>> wsurv;  // per range: p0, q0, p1, q1, ...
+  std::vector<std::vector<cuboid_root_wide>> wroots;
 };
 
 namespace cuboid {
@@ -92,14 +103,14 @@ static size_t result_block_bytes(uint32_t max_ranges, size_t n_counts) {
   return kHdrBytes + (size_t)max_ranges * sizeof(unsigned long long) + n_counts * sizeof(unsigned long long);
 }
 
-LaunchShape launch_shape(const cuboid_tables* t, bool count_steps) {
+LaunchShape launch_shape(const cuboid_tables* t, bool count_steps, bool wide) {
   const cuboid_tuning& T = t->tuning;
   LaunchShape L;
   L.threads = T.block_threads ? T.block_threads : kDefaultThreads;
-  L.row_lanes = (count_steps || !T.row_lanes) ? 32u : T.row_lanes;
+  L.row_lanes = (count_steps || wide || !T.row_lanes) ? 32u : T.row_lanes;
   const uint32_t ctas = T.ctas_per_sm ? T.ctas_per_sm : kDefaultCtasPerSm;
   const int smem_sm = t->smem_per_sm, smem_blk = t->smem_per_block;
-  const size_t fixed = sieve_smem_bytes(0, t->n, L.threads, L.row_lanes);
+  const size_t fixed = sieve_smem_bytes(0, t->n, L.threads, L.row_lanes, wide);
   // (128 bytes left for the kernel's static shared memory: the staging barrier)
   size_t per_cta = std::min<size_t>((size_t)smem_blk - 128, (size_t)smem_sm / ctas - 1024);
   size_t table_budget = per_cta > fixed ? per_cta - fixed : 0;
@@ -126,7 +137,7 @@ LaunchShape launch_shape(const cuboid_tables* t, bool count_steps) {
       L.n_hot = c;
       break;
     }
-  L.smem = sieve_smem_bytes(L.smem_words, t->n, L.threads, L.row_lanes);
+  L.smem = sieve_smem_bytes(L.smem_words, t->n, L.threads, L.row_lanes, wide);
   L.blocks = (uint32_t)t->sms * ctas;
   const uint32_t tpw = T.tiles_per_warp ? T.tiles_per_warp : kDefaultTilesPerWarp;
   L.target_tiles = L.blocks * (L.threads / 32) * tpw;
@@ -328,6 +339,7 @@ static void result_release(cuboid_result* r) {
     cudaFree(r->d_surv_range);
     cudaFree(r->d_roots);
     cudaFree(r->d_root_range);
+    cudaFree(r->d_base);
     cudaFreeHost(r->h_block);
     cudaFreeHost(r->h_ranges);
   }
@@ -428,11 +440,125 @@ int sieve_into(cuboid_result* r, const cuboid_range* ranges, uint32_t n, uint32_
   r->n_ranges = n;
   r->downloaded = false;
   r->fetched = false;
+  r->wide = false;
   e = run_kernels(r, d_ranges, h_ranges, n, mode, s);
   if (e != cudaSuccess) return status_from_cuda(e);
   if (download) return enqueue_download(r, s);
   e = cudaEventRecord(r->done, s);
   return status_from_cuda(e);
+}
+
+// ---- 64-bit ranges
+
+constexpr uint64_t k2p32 = 1ull << 32;
+
+// The pieces of a 64-bit range (cuboid.h, "64-bit ranges"): 32-bit ranges whose
+// coordinates are relative to bases (two per piece: added to p, added to q).
+static int wide_pieces(const cuboid_range_wide& R, std::vector<cuboid_range>& pieces,
+                       std::vector<unsigned long long>& bases) {
+  const uint32_t fl = R.flags;
+  if (R.reserved != 0 || (fl & ~0xFu) || ((fl & CUBOID_ROWS_P) && (fl & CUBOID_ROWS_Q))) return CUBOID_EINVAL;
+  if (R.p_lo == 0 || R.q_lo == 0 || R.p_lo > R.p_hi || R.q_lo > R.q_hi || R.p_hi >= CUBOID_WIDE_LIMIT ||
+      R.q_hi >= CUBOID_WIDE_LIMIT)
+    return CUBOID_ERANGE;
+  bool rows_q;
+  if (fl & CUBOID_ROWS_P) {
+    if (R.p_hi >= k2p32) return CUBOID_ERANGE;
+    rows_q = false;
+  } else if (fl & CUBOID_ROWS_Q) {
+    if (R.q_hi >= k2p32) return CUBOID_ERANGE;
+    rows_q = true;
+  } else if (R.p_hi < k2p32 && R.q_hi < k2p32) {  // a 32-bit range
+    pieces.push_back(cuboid_range{(uint32_t)R.p_lo, (uint32_t)R.p_hi, (uint32_t)R.q_lo, (uint32_t)R.q_hi, fl, 0u});
+    bases.push_back(0ull);
+    bases.push_back(0ull);
+    return CUBOID_OK;
+  } else if (R.p_hi < k2p32) {
+    rows_q = false;
+  } else if (R.q_hi < k2p32) {
+    rows_q = true;
+  } else {
+    return CUBOID_ERANGE;  // no coordinate below 2^32 to index the rows
+  }
+  const uint32_t x_lo = (uint32_t)(rows_q ? R.q_lo : R.p_lo), x_hi = (uint32_t)(rows_q ? R.q_hi : R.p_hi);
+  const uint64_t y_lo = rows_q ? R.p_lo : R.q_lo, y_hi = rows_q ? R.p_hi : R.q_hi;
+  const uint32_t row_flag = rows_q ? CUBOID_ROWS_Q : CUBOID_ROWS_P;
+  auto add = [&](uint64_t lo, uint64_t hi, uint64_t base, uint32_t flags) {
+    const uint32_t a = (uint32_t)(lo - base), b = (uint32_t)(hi - base);
+    pieces.push_back(rows_q ? cuboid_range{a, b, x_lo, x_hi, flags, 0u} : cuboid_range{x_lo, x_hi, a, b, flags, 0u});
+    bases.push_back(rows_q ? base : 0ull);
+    bases.push_back(rows_q ? 0ull : base);
+  };
+  // the values below 2^32: a 32-bit piece with the range's own restrictions
+  if (y_lo < k2p32)
+    add(y_lo, std::min<uint64_t>(y_hi, k2p32 - 1), 0ull, (fl & (CUBOID_Q_LT_P | CUBOID_ALLOW_DIAGONAL)) | row_flag);
+  // above 2^32 every y exceeds every row value: no diagonal pair, and q < p holds on all of
+  // a piece (rows of q, y = p) or on none of it (rows of p, y = q)
+  if ((fl & CUBOID_Q_LT_P) && !rows_q) return CUBOID_OK;
+  for (uint64_t start = std::max<uint64_t>(y_lo, k2p32); start <= y_hi;) {
+    const uint64_t base = (start & ~63ull) - 64;  // relative start in [64, 128)
+    const uint64_t end = std::min<uint64_t>(y_hi, base + 0xFFFFFFFFull);
+    add(start, end, base, row_flag);
+    start = end + 1;
+  }
+  return CUBOID_OK;
+}
+
+// Per piece a plan and a sieve launch (the first plan clears the header), then one root
+// test whose records are offset by the pieces' bases.
+static cudaError_t run_kernels_wide(cuboid_result* r, const std::vector<cuboid_range>& pieces, cudaStream_t s) {
+  const LaunchShape L = launch_shape(r->t, false, true);
+  cudaError_t e = sieve_set_smem_limit(false, L.smem);
+  if (e != cudaSuccess) return e;
+  const uint32_t n = (uint32_t)pieces.size();
+  if (n == 0) return launch_reset(r->d_hdr, 0, s);
+  r->timed_launches = 0;
+  for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
+    e = launch_plan(nullptr, i, 1, r->d_hdr, r->d_plan, r->d_counts, r->d_npairs, r->t->n, L.target_tiles, s,
+                    i == 0, L.row_lanes, &pieces[i]);
+    SieveArgs sa = sieve_args(r, L, i, 1);
+    sa.y_base = r->h_base[2 * (size_t)i] + r->h_base[2 * (size_t)i + 1];  // one of the two is 0
+    if (e == cudaSuccess) e = launch_sieve(sa, false, L.blocks, L.threads, L.smem, s, true);
+  }
+  if (e == cudaSuccess) {
+    VerifyArgs v = verify_args(r, false);
+    v.base = r->d_base;
+    e = launch_verify(v, verify_blocks(r->t), s, true);
+  }
+  return e;
+}
+
+// Per 64-bit range: counts and pair totals summed over its pieces, records made absolute.
+static void wide_collect(cuboid_result* r) {
+  const uint32_t np = r->t->n;
+  r->wcounts.assign((size_t)r->n_wide * np, 0);
+  r->wnpairs.assign(r->n_wide, 0);
+  r->wsurv.assign(r->n_wide, {});
+  r->wroots.assign(r->n_wide, {});
+  std::vector<std::vector<std::pair<uint64_t, uint64_t>>> sv(r->n_wide);
+  for (uint32_t k = 0; k < r->n_ranges; ++k) {
+    const uint32_t u = r->piece_of[k];
+    const uint64_t bp = r->h_base[2 * (size_t)k], bq = r->h_base[2 * (size_t)k + 1];
+    for (uint32_t i = 0; i < np; ++i) r->wcounts[(size_t)u * np + i] += r->counts[(size_t)k * np + i];
+    r->wnpairs[u] += r->npairs[k];
+    for (uint64_t rec : r->surv[k]) sv[u].push_back({(rec >> 32) + bp, (uint32_t)rec + bq});
+    for (const cuboid_root& x : r->roots[k])
+      r->wroots[u].push_back(cuboid_root_wide{x.p + bp, x.q + bq, x.t_lo, x.t_hi});
+  }
+  for (uint32_t u = 0; u < r->n_wide; ++u) {
+    std::sort(sv[u].begin(), sv[u].end());
+    r->wsurv[u].reserve(2 * sv[u].size());
+    for (const auto& pq : sv[u]) {
+      r->wsurv[u].push_back(pq.first);
+      r->wsurv[u].push_back(pq.second);
+    }
+    std::sort(r->wroots[u].begin(), r->wroots[u].end(), [](const cuboid_root_wide& a, const cuboid_root_wide& b) {
+      if (a.p != b.p) return a.p < b.p;
+      if (a.q != b.q) return a.q < b.q;
+      if (a.t_hi != b.t_hi) return a.t_hi < b.t_hi;
+      return a.t_lo < b.t_lo;
+    });
+  }
 }
 
 int result_wait(cuboid_result* r) {
@@ -498,6 +624,7 @@ int result_wait(cuboid_result* r) {
   else if (H.status & kStatusVerifyFail) st = CUBOID_EVERIFY;
   else if (H.status & kStatusBadRange) st = CUBOID_ERANGE;
   else if (H.status & (kStatusSurvOverflow | kStatusRootOverflow)) st = CUBOID_EOVERFLOW;
+  if (r->wide) wide_collect(r);
   r->wait_status = st;
   r->fetched = true;
   return st;
@@ -601,7 +728,7 @@ extern "C" int cuboid_result_wait(cuboid_result* res) { return result_wait(res);
 extern "C" int cuboid_result_get(const cuboid_result* res, uint32_t range_idx, uint64_t* n_pairs,
                                  uint64_t* counts, uint64_t* n_surv, const uint64_t** surv,
                                  uint64_t* n_roots, const cuboid_root** roots) {
-  if (!res || !res->fetched) return CUBOID_EINVAL;
+  if (!res || !res->fetched || res->wide) return CUBOID_EINVAL;
   if (range_idx >= res->n_ranges) return CUBOID_EINVAL;
   const uint32_t np = res->t ? res->t->n : (uint32_t)(res->counts.size() / std::max<uint32_t>(res->n_ranges, 1));
   if (n_pairs) *n_pairs = res->npairs[range_idx];
@@ -610,6 +737,82 @@ extern "C" int cuboid_result_get(const cuboid_result* res, uint32_t range_idx, u
   if (surv) *surv = res->surv[range_idx].data();
   if (n_roots) *n_roots = res->roots[range_idx].size();
   if (roots) *roots = res->roots[range_idx].data();
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_wide_pieces(const cuboid_range_wide* r, cuboid_range* pieces, uint64_t* bases, uint32_t cap,
+                                  uint32_t* n) {
+  if (!r || !n || (cap && (!pieces || !bases))) return CUBOID_EINVAL;
+  std::vector<cuboid_range> pc;
+  std::vector<unsigned long long> bs;
+  const int st = wide_pieces(*r, pc, bs);
+  if (st != CUBOID_OK) return st;
+  *n = (uint32_t)pc.size();
+  if (pc.size() > cap) return CUBOID_EOVERFLOW;
+  if (!pc.empty()) {
+    std::memcpy(pieces, pc.data(), pc.size() * sizeof(cuboid_range));
+    for (size_t i = 0; i < bs.size(); ++i) bases[i] = bs[i];
+  }
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_sieve_wide(const cuboid_tables* t, const cuboid_range_wide* ranges, uint32_t n, void* stream,
+                                 cuboid_result** out) {
+  if (!t) return CUBOID_ENOTABLES;
+  if (!out || !ranges || n == 0) return CUBOID_EINVAL;
+  std::vector<cuboid_range> pieces;
+  std::vector<unsigned long long> bases;
+  std::vector<uint32_t> owner;
+  for (uint32_t i = 0; i < n; ++i) {
+    const size_t before = pieces.size();
+    const int st = wide_pieces(ranges[i], pieces, bases);
+    if (st != CUBOID_OK) return st;
+    owner.insert(owner.end(), pieces.size() - before, i);
+  }
+  if (pieces.size() >= 0xFFFFFFFFull) return CUBOID_ETOOLARGE;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return CUBOID_EINVAL;
+  cuboid_result* r = nullptr;
+  int st = result_create(t, std::max<uint32_t>((uint32_t)pieces.size(), 1u), 0, 0, &r);
+  if (st != CUBOID_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nb = std::max<size_t>(bases.size(), 2);
+  cudaError_t e = cudaMalloc(&r->d_base, nb * sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    r->d_base_cap = nb;
+    if (!bases.empty())
+      e = cudaMemcpyAsync(r->d_base, bases.data(), bases.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                          s);
+  }
+  r->wide = true;
+  r->n_wide = n;
+  r->piece_of = owner;
+  r->h_base = bases;
+  r->n_ranges = (uint32_t)pieces.size();
+  r->downloaded = false;
+  r->fetched = false;
+  if (e == cudaSuccess) e = run_kernels_wide(r, pieces, s);
+  st = e == cudaSuccess ? enqueue_download(r, s) : status_from_cuda(e);
+  if (st != CUBOID_OK) {
+    result_release(r);
+    return st;
+  }
+  *out = r;
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_result_get_wide(const cuboid_result* res, uint32_t range_idx, uint64_t* n_pairs,
+                                      uint64_t* counts, uint64_t* n_surv, const uint64_t** surv, uint64_t* n_roots,
+                                      const cuboid_root_wide** roots) {
+  if (!res || !res->fetched || !res->wide || range_idx >= res->n_wide) return CUBOID_EINVAL;
+  const uint32_t np = res->t->n;
+  if (n_pairs) *n_pairs = res->wnpairs[range_idx];
+  if (counts) std::memcpy(counts, res->wcounts.data() + (size_t)range_idx * np, np * sizeof(uint64_t));
+  if (n_surv) *n_surv = res->wsurv[range_idx].size() / 2;
+  if (surv) *surv = res->wsurv[range_idx].data();
+  if (n_roots) *n_roots = res->wroots[range_idx].size();
+  if (roots) *roots = res->wroots[range_idx].data();
   return CUBOID_OK;
 }
 
@@ -634,6 +837,78 @@ extern "C" int cuboid_result_free(cuboid_result* res) {
 
 // ------------------------------------------------------------------ exact root test on given pairs
 
+namespace cuboid {
+
+// The root test of n records (p << 32 | q) on the device, synchronous on s.  rng (or null):
+// each record's range index; base (or null): per range the values added to p and q.  Roots
+// come back unsorted with their range indices; fail: a survivor the test could not settle.
+static int verify_records(const std::vector<unsigned long long>& rec, const std::vector<uint32_t>* rng,
+                          const std::vector<unsigned long long>* base, cudaStream_t s,
+                          std::vector<cuboid_root>& out, std::vector<uint32_t>& out_range, bool& fail) {
+  const size_t n = rec.size();
+  cudaError_t e = verify_init_device();
+  if (e != cudaSuccess) return status_from_cuda(e);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t rcap = 5ull * n;  // at most five roots u of the quintic per pair
+  DevHeader* d_hdr = nullptr;
+  unsigned long long* d_surv = nullptr;
+  unsigned long long* d_base = nullptr;
+  uint32_t* d_rng = nullptr;
+  cuboid_root* d_roots = nullptr;
+  uint32_t* d_rr = nullptr;
+  e = cudaMalloc(&d_hdr, sizeof(DevHeader));
+  if (e == cudaSuccess) e = cudaMalloc(&d_surv, n * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&d_roots, rcap * sizeof(cuboid_root));
+  if (e == cudaSuccess) e = cudaMalloc(&d_rr, rcap * sizeof(uint32_t));
+  if (e == cudaSuccess && rng) e = cudaMalloc(&d_rng, n * sizeof(uint32_t));
+  if (e == cudaSuccess && base) e = cudaMalloc(&d_base, base->size() * sizeof(unsigned long long));
+  DevHeader H{};
+  H.n_surv = n;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_hdr, &H, sizeof(H), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_surv, rec.data(), n * sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && rng)
+    e = cudaMemcpyAsync(d_rng, rng->data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && base)
+    e = cudaMemcpyAsync(d_base, base->data(), base->size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    VerifyArgs v;
+    v.surv = d_surv;
+    v.surv_range = d_rng;
+    v.surv_cap = n;
+    v.hdr = d_hdr;
+    v.roots = d_roots;
+    v.root_range = d_rr;
+    v.root_cap = rcap;
+    v.base = d_base;
+    e = launch_verify(v, (uint32_t)sms * 2, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&H, d_hdr, sizeof(H), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  out.clear();
+  out_range.clear();
+  if (e == cudaSuccess && H.n_roots) {
+    out.resize(std::min<uint64_t>(H.n_roots, rcap));
+    out_range.resize(out.size());
+    e = cudaMemcpy(out.data(), d_roots, out.size() * sizeof(cuboid_root), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(out_range.data(), d_rr, out.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  }
+  cudaFree(d_hdr);
+  cudaFree(d_surv);
+  cudaFree(d_roots);
+  cudaFree(d_rr);
+  cudaFree(d_rng);
+  cudaFree(d_base);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  fail = (H.status & kStatusVerifyFail) != 0;
+  return CUBOID_OK;
+}
+
+}  // namespace cuboid
+
 extern "C" int cuboid_verify_pairs(const uint32_t* p, const uint32_t* q, uint32_t n, void* stream,
                                    cuboid_root* roots_out, uint64_t cap, uint64_t* n_roots) {
   if (!p || !q || !n_roots || (cap && !roots_out)) return CUBOID_EINVAL;
@@ -641,51 +916,13 @@ extern "C" int cuboid_verify_pairs(const uint32_t* p, const uint32_t* q, uint32_
     if (p[i] == 0 || q[i] == 0) return CUBOID_EINVAL;
   *n_roots = 0;
   if (n == 0) return CUBOID_OK;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = verify_init_device();
-  if (e != cudaSuccess) return status_from_cuda(e);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t rcap = std::max<uint64_t>(cap, 5ull * n);
   std::vector<unsigned long long> rec(n);
   for (uint32_t i = 0; i < n; ++i) rec[i] = ((unsigned long long)p[i] << 32) | q[i];
-  DevHeader* d_hdr = nullptr;
-  unsigned long long* d_surv = nullptr;
-  cuboid_root* d_roots = nullptr;
-  uint32_t* d_rr = nullptr;
-  e = cudaMalloc(&d_hdr, sizeof(DevHeader));
-  if (e == cudaSuccess) e = cudaMalloc(&d_surv, n * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc(&d_roots, rcap * sizeof(cuboid_root));
-  if (e == cudaSuccess) e = cudaMalloc(&d_rr, rcap * sizeof(uint32_t));
-  DevHeader H{};
-  H.n_surv = n;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_hdr, &H, sizeof(H), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_surv, rec.data(), n * sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) {
-    VerifyArgs v;
-    v.surv = d_surv;
-    v.surv_range = nullptr;
-    v.surv_cap = n;
-    v.hdr = d_hdr;
-    v.roots = d_roots;
-    v.root_range = d_rr;
-    v.root_cap = rcap;
-    e = launch_verify(v, (uint32_t)sms * 2, s);
-  }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&H, d_hdr, sizeof(H), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   std::vector<cuboid_root> out;
-  if (e == cudaSuccess && H.n_roots) {
-    out.resize(std::min<uint64_t>(H.n_roots, rcap));
-    e = cudaMemcpy(out.data(), d_roots, out.size() * sizeof(cuboid_root), cudaMemcpyDeviceToHost);
-  }
-  cudaFree(d_hdr);
-  cudaFree(d_surv);
-  cudaFree(d_roots);
-  cudaFree(d_rr);
-  if (e != cudaSuccess) return status_from_cuda(e);
+  std::vector<uint32_t> rr;
+  bool fail = false;
+  const int st = verify_records(rec, nullptr, nullptr, (cudaStream_t)stream, out, rr, fail);
+  if (st != CUBOID_OK) return st;
   std::sort(out.begin(), out.end(), [](const cuboid_root& a, const cuboid_root& b) {
     if (a.p != b.p) return a.p < b.p;
     if (a.q != b.q) return a.q < b.q;
@@ -693,9 +930,49 @@ extern "C" int cuboid_verify_pairs(const uint32_t* p, const uint32_t* q, uint32_
     return a.t_lo < b.t_lo;
   });
   *n_roots = out.size();
-  if (H.status & kStatusVerifyFail) return CUBOID_EVERIFY;
+  if (fail) return CUBOID_EVERIFY;
   if (out.size() > cap) return CUBOID_EOVERFLOW;
   if (!out.empty()) std::memcpy(roots_out, out.data(), out.size() * sizeof(cuboid_root));
+  return CUBOID_OK;
+}
+
+static bool wide_root_less(const cuboid_root_wide& a, const cuboid_root_wide& b) {
+  if (a.p != b.p) return a.p < b.p;
+  if (a.q != b.q) return a.q < b.q;
+  if (a.t_hi != b.t_hi) return a.t_hi < b.t_hi;
+  return a.t_lo < b.t_lo;
+}
+
+extern "C" int cuboid_verify_pairs_wide(const uint64_t* p, const uint64_t* q, uint32_t n, void* stream,
+                                        cuboid_root_wide* roots_out, uint64_t cap, uint64_t* n_roots) {
+  if (!p || !q || !n_roots || (cap && !roots_out)) return CUBOID_EINVAL;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (p[i] == 0 || q[i] == 0) return CUBOID_EINVAL;
+    if (p[i] >= CUBOID_WIDE_LIMIT || q[i] >= CUBOID_WIDE_LIMIT) return CUBOID_ERANGE;
+  }
+  *n_roots = 0;
+  if (n == 0) return CUBOID_OK;
+  // each pair is its own "range" whose base is the pair itself (records are zero)
+  std::vector<unsigned long long> rec(n, 0ull), base(2 * (size_t)n);
+  std::vector<uint32_t> rng(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    rng[i] = i;
+    base[2 * (size_t)i] = p[i];
+    base[2 * (size_t)i + 1] = q[i];
+  }
+  std::vector<cuboid_root> out;
+  std::vector<uint32_t> rr;
+  bool fail = false;
+  const int st = verify_records(rec, &rng, &base, (cudaStream_t)stream, out, rr, fail);
+  if (st != CUBOID_OK) return st;
+  std::vector<cuboid_root_wide> w(out.size());
+  for (size_t i = 0; i < out.size(); ++i)
+    w[i] = cuboid_root_wide{out[i].p + p[rr[i]], out[i].q + q[rr[i]], out[i].t_lo, out[i].t_hi};
+  std::sort(w.begin(), w.end(), wide_root_less);
+  *n_roots = w.size();
+  if (fail) return CUBOID_EVERIFY;
+  if (w.size() > cap) return CUBOID_EOVERFLOW;
+  if (!w.empty()) std::memcpy(roots_out, w.data(), w.size() * sizeof(cuboid_root_wide));
   return CUBOID_OK;
 }
 

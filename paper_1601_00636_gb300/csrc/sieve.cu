@@ -95,12 +95,13 @@ __device__ __forceinline__ uint32_t mod_min(uint32_t n, uint32_t r, uint32_t mag
 
 // Up to 32 queued words {x, y0, alive lo, alive hi} (one per lane) of range `range` go
 // through the primes [first, n) with a warp-uniform early exit; then the survivors are
-// compacted.
-template <bool kSteps>
+// compacted.  kWide: y0 is relative to the piece's base, whose residues are s_ybr.
+template <bool kSteps, bool kWide>
 __device__ __forceinline__ void cold_batch(const SieveArgs& a, const PrimeInfo* s_info, const uint32_t* s_tab,
-                                           uint32_t* wcnt, const uint4* q, uint32_t cnt, uint32_t first,
-                                           bool rows_q, uint32_t range, uint32_t lane, WarpState& ws,
-                                           unsigned long long& st_wsteps, unsigned long long& st_warpsteps) {
+                                           const uint32_t* s_ybr, uint32_t* wcnt, const uint4* q, uint32_t cnt,
+                                           uint32_t first, bool rows_q, uint32_t range, uint32_t lane,
+                                           WarpState& ws, unsigned long long& st_wsteps,
+                                           unsigned long long& st_warpsteps) {
   const uint4 e = lane < cnt ? q[lane] : make_uint4(0u, 0u, 0u, 0u);
   const uint32_t x = e.x, y0 = e.y;
   uint32_t al = e.z, ah = e.w;
@@ -110,7 +111,11 @@ __device__ __forceinline__ void cold_batch(const SieveArgs& a, const PrimeInfo* 
     if (!__any_sync(FULL, (al | ah) != 0u)) break;
     const PrimeInfo pi = s_info[i];
     const uint32_t ro = pi.off + mod_min(x, pi.r, pi.magic) * pi.W;
-    const uint32_t s = mod_min(y0, pi.r, pi.magic);
+    uint32_t s = mod_min(y0, pi.r, pi.magic);
+    if constexpr (kWide) {  // (y_base + y0) mod r
+      s += s_ybr[i];
+      s = min(s, s - pi.r);
+    }
     const uint32_t wi = ro + (s >> 5);
     uint32_t w0, w1, w2;
     if (i < a.n_smem_primes) {
@@ -166,14 +171,15 @@ __device__ __forceinline__ void cold_batch(const SieveArgs& a, const PrimeInfo* 
 }
 
 // Process full batches of 32 queued words (all of them when `all`).
-template <bool kSteps>
+template <bool kSteps, bool kWide>
 __device__ __forceinline__ void drain(const SieveArgs& a, const PrimeInfo* s_info, const uint32_t* s_tab,
-                                      uint32_t* wcnt, uint4* q, uint32_t& qn, uint32_t first, bool rows_q,
-                                      uint32_t range, uint32_t lane, WarpState& ws, unsigned long long& st_wsteps,
-                                      unsigned long long& st_warpsteps, bool all) {
+                                      const uint32_t* s_ybr, uint32_t* wcnt, uint4* q, uint32_t& qn,
+                                      uint32_t first, bool rows_q, uint32_t range, uint32_t lane, WarpState& ws,
+                                      unsigned long long& st_wsteps, unsigned long long& st_warpsteps, bool all) {
   while (qn >= 32 || (all && qn > 0)) {
     const uint32_t cnt = qn < 32 ? qn : 32;
-    cold_batch<kSteps>(a, s_info, s_tab, wcnt, q, cnt, first, rows_q, range, lane, ws, st_wsteps, st_warpsteps);
+    cold_batch<kSteps, kWide>(a, s_info, s_tab, s_ybr, wcnt, q, cnt, first, rows_q, range, lane, ws, st_wsteps,
+                              st_warpsteps);
     const uint32_t rest = qn - cnt;
     uint4 e = make_uint4(0u, 0u, 0u, 0u);
     if (lane < rest) e = q[32 + lane];
@@ -193,8 +199,12 @@ __device__ __forceinline__ void drain(const SieveArgs& a, const PrimeInfo* s_inf
 // one subtile, each lane a pair of adjacent words at a time, lanes on pairs G apart.  G = 32 is one subtile per warp; smaller groups
 // share the per-row setup (factors of the row value, residues of the hot primes) among
 // fewer words, which pays on short rows.
-template <bool kSteps, int K, int kMaxThreads, int G>
+// kWide: the launch sieves one piece of a 64-bit range (SieveArgs::y_base): the residues of
+// y_base modulo the table primes (per CTA) and modulo the row's factors (per row) are added
+// to those of the relative y; whole-warp rows only.
+template <bool kSteps, int K, int kMaxThreads, int G, bool kWide = false>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
+  static_assert(!kWide || G == 32, "64-bit pieces use whole-warp rows");
   static_assert(G == 8 || G == 16 || G == 32, "lanes per row");
   constexpr uint32_t NG = 32 / G;                 // subtiles per tile (groups per warp)
   constexpr uint32_t kStride = 128u * G;          // a lane's next pair of words starts 2 G words further on
@@ -220,6 +230,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   uint32_t* s_foff = reinterpret_cast<uint32_t*>(s_mtab + kMaskTab);                       // [kPeriodicBelow]
   uint32_t* s_fmag_all = s_foff + kPeriodicBelow;                                                       // [warps][NG][kMaxFactors]
   uint32_t* s_cnt_all = s_fmag_all + warps * NG * kMaxFactors;                              // [warps][n]
+  uint32_t* s_ybr = s_cnt_all + warps * n;                  // [n] (kWide): y_base mod r
+  uint32_t* s_fyb_all = s_ybr + n;                          // [warps][NG][kMaxFactors] (kWide): y_base mod f
   __shared__ __align__(8) unsigned long long s_bar;  // completion of the bulk copies
   __shared__ TilePlan s_self_plan;                    // the single range's plan (self_plan)
   __shared__ unsigned long long s_self_total;
@@ -280,11 +292,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     mbar_wait_parity(bar, 0u, kStageSpins);
     return;
   }
+  if constexpr (kWide) {  // residues of the piece's base, effective order (hot primes first)
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) s_ybr[i] = (uint32_t)(a.y_base % s_info[i].r);
+    __syncthreads();
+  }
   pdl_wait();     // the plan (header, tile plans, zeroed counts) is complete from here on
   pdl_trigger();  // the root-test grid may be scheduled as CTAs of this grid retire
 
   uint4* s_fac = s_fac_all + (wid * NG + g) * kMaxFactors;        // this group's factors
   uint32_t* s_fmag = s_fmag_all + (wid * NG + g) * kMaxFactors;
+  uint32_t* s_fyb = s_fyb_all + (wid * NG + g) * kMaxFactors;
   uint4* s_queue = s_queue_all + wid * kQueue;
   uint32_t* wcnt = s_cnt_all + wid * n;
   const uint32_t count = a.self_plan ? 1u : (a.range_count == kNoRange ? a.hdr->n_ranges : a.range_count);
@@ -343,8 +360,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     const unsigned long long tbeg = (k == a.range_first) ? 0ull : a.plan[k - 1].tile_end;
     if (k != ws.cur_range || ws.tiles_since_flush >= kFlushTiles) {
       fold();
-      drain<kSteps>(a, s_info, s_tab, wcnt, s_queue, qn, K, q_rows, ws.cur_range, lane, ws, st_wsteps,
-                    st_warpsteps, true);
+      drain<kSteps, kWide>(a, s_info, s_tab, s_ybr, wcnt, s_queue, qn, K, q_rows, ws.cur_range, lane, ws,
+                           st_wsteps, st_warpsteps, true);
       flush_counts(ws, wcnt, a, lane);
       ws.cur_range = k;
     }
@@ -352,7 +369,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
 
     const bool rows_q = P.flags & kRowsQ;
     q_rows = rows_q;
-    const bool tri = P.flags & CUBOID_Q_LT_P;
+    const bool tri = !kWide && (P.flags & CUBOID_Q_LT_P);  // a 64-bit piece lies above every row value
     const uint32_t diag = (P.flags & CUBOID_ALLOW_DIAGONAL) ? 1u : 0u;
     const uint32_t wbox_lo = P.y_lo >> 6;
     const uint32_t nw = (P.y_hi >> 6) - wbox_lo + 1;
@@ -403,7 +420,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     if (kSteps) st_tiles++;
     const unsigned long long lo_mask = FULL64 << (uint32_t)(ylo & 63);
     const unsigned long long hi_mask = FULL64 >> (63 - (uint32_t)(yhi & 63));
-    const uint32_t dword = x >> 6;
+    const uint32_t dword = kWide ? 0xFFFFFFFFu : x >> 6;  // past every word: no diagonal in a 64-bit piece
     const uint32_t dbit_lo = (x & 32) ? 0u : 1u << (x & 31), dbit_hi = (x & 32) ? 1u << (x & 31) : 0u;
 
     // ---- distinct odd prime factors of x (trial division shared by the group's lanes)
@@ -453,6 +470,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           s_fac[pos] = make_uint4(f, mod_min(kStride, f, tp.lim), f < kPeriodicBelow ? s_foff[f] : kBitTab,
                                   f < kPeriodicBelow ? f - 1 : 128u);
           s_fmag[pos] = tp.lim;  // floor(2^32 / f) for odd f > 1
+          if constexpr (kWide) s_fyb[pos] = (uint32_t)(a.y_base % f);
         }
 #pragma unroll
         for (int d = G / 2; d; d >>= 1) pw *= __shfl_xor_sync(FULL, pw, d);  // within the group
@@ -468,6 +486,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           s_fac[nfo] = make_uint4(m, mod_min(kStride, m, mag), m < kPeriodicBelow ? s_foff[m] : kBitTab,
                                   m < kPeriodicBelow ? m - 1 : 128u);
           s_fmag[nfo] = mag;
+          if constexpr (kWide) s_fyb[nfo] = (uint32_t)(a.y_base % m);
         }
         ++nfo;
       }
@@ -485,7 +504,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
       tf[i] = 128u;  // inert entry
       if ((uint32_t)i < nfo) {
         const uint32_t f = s_fac[i].x;
-        const uint32_t r = mod_min(y0f, f, s_fmag[i]);
+        uint32_t r = mod_min(y0f, f, s_fmag[i]);
+        if constexpr (kWide) {  // (y_base + y0) mod f; f may exceed 2^31
+          const unsigned long long rr = (unsigned long long)r + s_fyb[i];
+          r = (uint32_t)(rr >= f ? rr - f : rr);
+        }
         tf[i] = r ? f - r : 0u;
       }
     }
@@ -496,7 +519,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
 #pragma unroll
     for (int h = 0; h < K; ++h) {
       rb[h] = a.hot_off[h] + mod_min(x, a.hot_r[h], a.hot_magic[h]) * a.hot_W[h];
-      sh[h] = mod_min(y0f, a.hot_r[h], a.hot_magic[h]);
+      uint32_t s0 = mod_min(y0f, a.hot_r[h], a.hot_magic[h]);
+      if constexpr (kWide) {
+        s0 += s_ybr[h];
+        s0 = min(s0, s0 - a.hot_r[h]);
+      }
+      sh[h] = s0;
     }
 
     const uint32_t emask = has2 ? 0xAAAAAAAAu : FULL;  // x even: y0 is even, so even y sit at even bits
@@ -534,8 +562,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         if (al | ah) s_queue[qn + __popc(bal & lanemask_lt)] = make_uint4(x, y0, al, ah);
         qn += __popc(bal);
         __syncwarp();
-        drain<kSteps>(a, s_info, s_tab, wcnt, s_queue, qn, K, rows_q, k, lane, ws, st_wsteps, st_warpsteps,
-                      false);
+        drain<kSteps, kWide>(a, s_info, s_tab, s_ybr, wcnt, s_queue, qn, K, rows_q, k, lane, ws, st_wsteps,
+                             st_warpsteps, false);
       }
     };
     uint32_t wb = wbeg + 2 * gl;
@@ -558,7 +586,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         }
         for (uint32_t i = kFacRegs; i < nfo; ++i) {
           const uint4 fc = s_fac[i];
-          const uint32_t s = mod_min(wA << 6, fc.x, s_fmag[i]);
+          uint32_t s = mod_min(wA << 6, fc.x, s_fmag[i]);
+          if constexpr (kWide) {
+            const unsigned long long ss = (unsigned long long)s + s_fyb[i];
+            s = (uint32_t)(ss >= fc.x ? ss - fc.x : ss);
+          }
           const uint32_t t = s ? fc.x - s : 0u;
           const uint4 mk = s_mtab[fc.z + min(t, fc.w)];
           m.x |= mk.x;
@@ -595,8 +627,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     next = __shfl_sync(FULL, next, 0);
   }
   fold();
-  drain<kSteps>(a, s_info, s_tab, wcnt, s_queue, qn, K, q_rows, ws.cur_range, lane, ws, st_wsteps, st_warpsteps,
-                true);
+  drain<kSteps, kWide>(a, s_info, s_tab, s_ybr, wcnt, s_queue, qn, K, q_rows, ws.cur_range, lane, ws, st_wsteps,
+                       st_warpsteps, true);
   flush_counts(ws, wcnt, a, lane);
   if (kSteps) {
     const unsigned long long w = warp_sum_u64(st_words), s = warp_sum_u64(st_wsteps);
@@ -609,54 +641,57 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   }
 }
 
-template <bool S, int M, int G>
+template <bool S, int M, int G, bool W>
 cudaError_t set_attr_g(size_t bytes) {
   const int b = (int)bytes;
-  cudaError_t e = cudaFuncSetAttribute(k_sieve<S, 0, M, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaError_t e = cudaFuncSetAttribute(k_sieve<S, 0, M, G, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sieve<S, 2, M, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    e = cudaFuncSetAttribute(k_sieve<S, 2, M, G, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sieve<S, 4, M, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    e = cudaFuncSetAttribute(k_sieve<S, 4, M, G, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sieve<S, 5, M, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    e = cudaFuncSetAttribute(k_sieve<S, 5, M, G, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sieve<S, 6, M, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    e = cudaFuncSetAttribute(k_sieve<S, 6, M, G, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   return e;
 }
 
 // The step-counting build exists for whole-warp rows only (the counts do not depend on
-// the lanes per row).
+// the lanes per row), and so does the build for pieces of 64-bit ranges.
 template <bool S>
 cudaError_t set_attr_all(size_t bytes) {
-  cudaError_t e = set_attr_g<S, 1024, 32>(bytes);
-  if (e == cudaSuccess) e = set_attr_g<S, 512, 32>(bytes);
+  cudaError_t e = set_attr_g<S, 1024, 32, false>(bytes);
+  if (e == cudaSuccess) e = set_attr_g<S, 512, 32, false>(bytes);
   if constexpr (!S) {
-    if (e == cudaSuccess) e = set_attr_g<S, 1024, 16>(bytes);
-    if (e == cudaSuccess) e = set_attr_g<S, 512, 16>(bytes);
-    if (e == cudaSuccess) e = set_attr_g<S, 1024, 8>(bytes);
-    if (e == cudaSuccess) e = set_attr_g<S, 512, 8>(bytes);
+    if (e == cudaSuccess) e = set_attr_g<S, 1024, 16, false>(bytes);
+    if (e == cudaSuccess) e = set_attr_g<S, 512, 16, false>(bytes);
+    if (e == cudaSuccess) e = set_attr_g<S, 1024, 8, false>(bytes);
+    if (e == cudaSuccess) e = set_attr_g<S, 512, 8, false>(bytes);
+    if (e == cudaSuccess) e = set_attr_g<S, 1024, 32, true>(bytes);
+    if (e == cudaSuccess) e = set_attr_g<S, 512, 32, true>(bytes);
   }
   return e;
 }
 
-template <bool S, int M, int G>
+template <bool S, int M, int G, bool W>
 cudaError_t launch_g(const SieveArgs& a, uint32_t blocks, uint32_t threads, size_t smem, cudaStream_t s, bool pdl) {
   switch (a.n_hot) {
-    case 6: return launch_ex(k_sieve<S, 6, M, G>, blocks, threads, smem, s, pdl, a);
-    case 5: return launch_ex(k_sieve<S, 5, M, G>, blocks, threads, smem, s, pdl, a);
-    case 4: return launch_ex(k_sieve<S, 4, M, G>, blocks, threads, smem, s, pdl, a);
-    case 2: return launch_ex(k_sieve<S, 2, M, G>, blocks, threads, smem, s, pdl, a);
-    default: return launch_ex(k_sieve<S, 0, M, G>, blocks, threads, smem, s, pdl, a);
+    case 6: return launch_ex(k_sieve<S, 6, M, G, W>, blocks, threads, smem, s, pdl, a);
+    case 5: return launch_ex(k_sieve<S, 5, M, G, W>, blocks, threads, smem, s, pdl, a);
+    case 4: return launch_ex(k_sieve<S, 4, M, G, W>, blocks, threads, smem, s, pdl, a);
+    case 2: return launch_ex(k_sieve<S, 2, M, G, W>, blocks, threads, smem, s, pdl, a);
+    default: return launch_ex(k_sieve<S, 0, M, G, W>, blocks, threads, smem, s, pdl, a);
   }
 }
 
 template <bool S, int M>
 cudaError_t launch_m(const SieveArgs& a, uint32_t blocks, uint32_t threads, size_t smem, cudaStream_t s, bool pdl) {
   if constexpr (!S) {
-    if (a.row_lanes == 8) return launch_g<S, M, 8>(a, blocks, threads, smem, s, pdl);
-    if (a.row_lanes == 16) return launch_g<S, M, 16>(a, blocks, threads, smem, s, pdl);
+    if (a.y_base) return launch_g<S, M, 32, true>(a, blocks, threads, smem, s, pdl);
+    if (a.row_lanes == 8) return launch_g<S, M, 8, false>(a, blocks, threads, smem, s, pdl);
+    if (a.row_lanes == 16) return launch_g<S, M, 16, false>(a, blocks, threads, smem, s, pdl);
   }
-  return launch_g<S, M, 32>(a, blocks, threads, smem, s, pdl);
+  return launch_g<S, M, 32, false>(a, blocks, threads, smem, s, pdl);
 }
 
 // The 128-register variant serves shapes with at most 512 threads per SM.
@@ -669,15 +704,17 @@ cudaError_t launch_k(const SieveArgs& a, uint32_t blocks, uint32_t threads, uint
 
 }  // namespace
 
-size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads, uint32_t row_lanes) {
+size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads, uint32_t row_lanes, bool wide) {
   const uint32_t warps = threads / 32;
   const uint32_t groups = 32 / (row_lanes ? row_lanes : 32);
+  const size_t wide_bytes =
+      wide ? (size_t)n_primes * sizeof(uint32_t) + (size_t)warps * groups * kMaxFactors * sizeof(uint32_t) : 0;
   return (((size_t)smem_words * 4 + 15) & ~(size_t)15) + (size_t)n_primes * sizeof(PrimeInfo) +
          (size_t)kTrialSmem * sizeof(TrialPrime) +
          (size_t)warps * groups * kMaxFactors * sizeof(uint4) +
          (size_t)warps * kQueue * sizeof(uint4) + kMaskTab * sizeof(uint4) + kPeriodicBelow * sizeof(uint32_t) +
          (size_t)warps * groups * kMaxFactors * sizeof(uint32_t) +
-         (size_t)warps * n_primes * sizeof(uint32_t);
+         (size_t)warps * n_primes * sizeof(uint32_t) + wide_bytes;
 }
 
 // The dynamic shared-memory limit is a per-device function attribute: raise it only when
@@ -698,6 +735,7 @@ cudaError_t sieve_set_smem_limit(bool count_steps, size_t bytes) {
 
 cudaError_t launch_sieve(const SieveArgs& a, bool count_steps, uint32_t blocks, uint32_t threads,
                          size_t smem, cudaStream_t s, bool pdl) {
+  if (a.y_base && (count_steps || a.row_lanes != 32 || a.self_plan)) return cudaErrorInvalidValue;
   const uint32_t per_sm = a.n_sms ? (blocks + a.n_sms - 1) / a.n_sms : 2;
   const cudaError_t e = count_steps ? launch_k<true>(a, blocks, threads, per_sm, smem, s, pdl)
                                     : launch_k<false>(a, blocks, threads, per_sm, smem, s, pdl);

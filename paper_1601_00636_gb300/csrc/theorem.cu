@@ -1,8 +1,8 @@
 // Theorem 1.1 on reported roots: a positive root t of Q_pq (coprime p != q) gives a perfect
 // cuboid exactly when t > p^2, t > p q, t > q^2 and (p^2 + t)(p q + t) > 2 t^2.  The last
-// inequality is p^3 q + (p^2 + p q) t > t^2; with t below 2^128 both sides stay below
-// 2^256 and are compared exactly in four 64-bit limbs.  Host code: roots are rare and
-// already on the host when this runs.
+// inequality is p^3 q + (p^2 + p q) t > t^2; with p, q below 2^40 and t below 2^128 both
+// sides stay below 2^256 and are compared exactly in four 64-bit limbs.  Host code: roots
+// are rare and already on the host when this runs.
 #include <cstdint>
 
 #include "cuboid_internal.cuh"
@@ -39,13 +39,21 @@ int cmp(const U256& x, const U256& y) {
   return 0;
 }
 
-bool holds(const cuboid_root& r) {
-  const u128 t = ((u128)r.t_hi << 64) | r.t_lo;
-  const uint64_t p = r.p, q = r.q;
+void add(U256& x, const U256& y) {
+  uint64_t c = 0;
+  for (int k = 0; k < 4; ++k) {
+    const u128 s = (u128)x.w[k] + y.w[k] + c;
+    x.w[k] = (uint64_t)s;
+    c = (uint64_t)(s >> 64);
+  }
+}
+
+// p, q < 2^40: p^2, pq, q^2 < 2^80; (p^2 + pq) t < 2^209, p^3 q < 2^160, t^2 < 2^256.
+bool holds(uint64_t p, uint64_t q, u128 t) {
   const u128 p2 = (u128)p * p, pq = (u128)p * q, q2 = (u128)q * q;
   if (t == 0 || !(t > p2) || !(t > pq) || !(t > q2)) return false;
-  U256 lhs = mul(p2 + pq, t);        // (p^2 + pq) t < 2^193
-  add_at(lhs, 0, p2 * pq);           // p^3 q < 2^128
+  U256 lhs = mul(p2 + pq, t);
+  add(lhs, mul(p2, pq));
   return cmp(lhs, mul(t, t)) > 0;
 }
 
@@ -53,6 +61,17 @@ bool holds(const cuboid_root& r) {
 
 extern "C" int cuboid_theorem11_flags(const cuboid_root* roots, uint64_t n, uint8_t* flags) {
   if (n && (!roots || !flags)) return CUBOID_EINVAL;
-  for (uint64_t i = 0; i < n; ++i) flags[i] = holds(roots[i]) ? 1 : 0;
+  for (uint64_t i = 0; i < n; ++i)
+    flags[i] = holds(roots[i].p, roots[i].q, ((u128)roots[i].t_hi << 64) | roots[i].t_lo) ? 1 : 0;
+  return CUBOID_OK;
+}
+
+extern "C" int cuboid_theorem11_flags_wide(const cuboid_root_wide* roots, uint64_t n, uint8_t* flags) {
+  if (n && (!roots || !flags)) return CUBOID_EINVAL;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (roots[i].p >= CUBOID_WIDE_LIMIT || roots[i].q >= CUBOID_WIDE_LIMIT) return CUBOID_ERANGE;
+  }
+  for (uint64_t i = 0; i < n; ++i)
+    flags[i] = holds(roots[i].p, roots[i].q, ((u128)roots[i].t_hi << 64) | roots[i].t_lo) ? 1 : 0;
   return CUBOID_OK;
 }

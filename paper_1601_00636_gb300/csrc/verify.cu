@@ -10,7 +10,8 @@
 // Exact arithmetic: R^(d)(u) for 0 <= u <= U is below 2^35 M^20 in absolute value, so
 // its residues modulo K primes m_j in (2^61, 2^62) with 61 K >= 37 + 20 bitlen(M)
 // determine it: all residues zero <=> the value is zero, and Garner's mixed-radix digits
-// compared with those of (prod m_j - 1)/2 give its sign.
+// compared with those of (prod m_j - 1)/2 give its sign.  p and q are below 2^40 (64-bit
+// ranges; 32-bit ones are a special case): U < 2^166 fits three 64-bit limbs and K <= 14.
 //
 // Isolation (exact, complete): the real roots of R^(4) (linear), R^(3), ..., R are
 // bracketed level by level.  If every root of R^(d+1) in [0, U] lies in a unit cell
@@ -30,7 +31,7 @@ namespace cuboid {
 namespace {
 
 typedef unsigned long long ull;
-constexpr int kMaxMod = 12;
+constexpr int kMaxMod = 14;  // 61 * 14 >= 37 + 20 * 40: M below 2^40
 constexpr int kMaxCells = 24;
 
 struct ModConst {
@@ -116,6 +117,16 @@ __device__ U192 dtou(double x) {
   if (bit && limb + 1 < 3) r.w[limb + 1] = mant >> (64 - bit);
   return r;
 }
+// a b for a, b < 2^96 (the product fits 192 bits).
+__device__ __forceinline__ U192 umul128(unsigned __int128 a, unsigned __int128 b) {
+  const ull a0 = (ull)a, a1 = (ull)(a >> 64), b0 = (ull)b, b1 = (ull)(b >> 64);
+  const unsigned __int128 l = (unsigned __int128)a0 * b0;
+  const unsigned __int128 m1 = (unsigned __int128)a0 * b1, m2 = (unsigned __int128)a1 * b0;
+  U192 r = U192{{(ull)l, (ull)(l >> 64), (ull)a1 * b1}};
+  r = uadd(r, U192{{0ull, (ull)m1, (ull)(m1 >> 64)}});
+  r = uadd(r, U192{{0ull, (ull)m2, (ull)(m2 >> 64)}});
+  return r;
+}
 // u mod m in Montgomery form.
 __device__ __forceinline__ ull umod_mont(const U192& u, const ModConst& M) {
   ull x = mmul(red64(u.w[0], M.m), M.r2, M);
@@ -135,7 +146,8 @@ struct Ctx {
 // a_0..a_5 of R (Eq. 1.1 with u = t^2) modulo m, Montgomery form.
 __device__ void r_coeffs_mod(ull p, ull q, const ModConst& M, ull a[6]) {
   const ull m = M.m;
-  const ull P = tomont(p * p, M), Q = tomont(q * q, M);
+  const ull pm = tomont(p, M), qm = tomont(q, M);  // p, q < 2^40 < 8 m
+  const ull P = mmul(pm, pm, M), Q = mmul(qm, qm, M);
   auto k = [&](ull v) { return tomont(v, M); };
   const ull P2 = mmul(P, P, M), P3 = mmul(P2, P, M), P4 = mmul(P3, P, M), P5 = mmul(P4, P, M);
   const ull Q2 = mmul(Q, Q, M), Q3 = mmul(Q2, Q, M), Q4 = mmul(Q3, Q, M), Q5 = mmul(Q4, Q, M);
@@ -181,9 +193,9 @@ __device__ __forceinline__ double falling(int k, int d) {
   return f;
 }
 
-__device__ void ctx_init(Ctx& C, uint32_t p, uint32_t q) {
-  const uint32_t M = p > q ? p : q;
-  const int bits = 32 - __clz(M);
+__device__ void ctx_init(Ctx& C, ull p, ull q) {
+  const ull M = p > q ? p : q;
+  const int bits = 64 - __clzll((long long)M);
   int K = (37 + 20 * bits + 60) / 61;
   if (K > kMaxMod) K = kMaxMod;
   C.K = K;
@@ -196,7 +208,7 @@ __device__ void ctx_init(Ctx& C, uint32_t p, uint32_t q) {
         C.co[j][d][kk] = mmul(a[kk], tomont((ull)falling(kk, d), Mc), Mc);
   }
   double a[6];
-  r_coeffs_f64(p, q, a);
+  r_coeffs_f64((double)p, (double)q, a);
   for (int d = 0; d < 5; ++d)
     for (int kk = d; kk <= 5; ++kk) C.dco[d][kk] = a[kk] * falling(kk, d);
 }
@@ -355,10 +367,10 @@ struct Isolator {
   }
 };
 
-// floor(sqrt(u)) for u < 2^136, as a 128-bit integer.
+// floor(sqrt(u)) for u < 2^168, as a 128-bit integer.
 __device__ unsigned __int128 isqrt192(const U192& u) {
   unsigned __int128 r = 0;
-  for (int bit = 68; bit >= 0; --bit) {
+  for (int bit = 83; bit >= 0; --bit) {
     const unsigned __int128 c = r | ((unsigned __int128)1 << bit);
     // c^2 as U192
     const ull c0 = (ull)c, c1 = (ull)(c >> 64);
@@ -389,13 +401,13 @@ __global__ void __launch_bounds__(64) k_verify(VerifyArgs a) {
   for (ull idx = blockIdx.x * (ull)blockDim.x + threadIdx.x; idx < n;
        idx += (ull)gridDim.x * blockDim.x) {
     const ull rec = a.surv[idx];
-    const uint32_t p = (uint32_t)(rec >> 32), q = (uint32_t)rec;
+    const uint32_t p32 = (uint32_t)(rec >> 32), q32 = (uint32_t)rec;  // relative to the range's base
+    const uint32_t k = a.surv_range ? a.surv_range[idx] : 0u;
+    const ull p = p32 + (a.base ? a.base[2 * (ull)k] : 0ull), q = q32 + (a.base ? a.base[2 * (ull)k + 1] : 0ull);
     ctx_init(C, p, q);
     const ull M = p > q ? p : q;
-    const unsigned __int128 M4 = (unsigned __int128)(M * M) * (M * M);
-    const unsigned __int128 lo45 = (unsigned __int128)(ull)M4 * 45ull;
-    const unsigned __int128 hi45 = (unsigned __int128)(ull)(M4 >> 64) * 45ull + (lo45 >> 64);
-    iso.U = U192{{(ull)lo45, (ull)hi45, (ull)(hi45 >> 64)}};
+    const unsigned __int128 M2 = (unsigned __int128)M * M;  // < 2^80
+    iso.U = umul128(M2 * 45u, M2);                           // 45 M^4 < 2^166
     iso.run();
     if (iso.fail) atomicOr(&a.hdr->status, kStatusVerifyFail);
     for (int i = 0; i < iso.nroots; ++i) {
@@ -411,7 +423,7 @@ __global__ void __launch_bounds__(64) k_verify(VerifyArgs a) {
       if (ucmp(sq, iso.roots[i]) != 0 || t == 0) continue;
       const ull slot = atomicAdd(&a.hdr->n_roots, 1ull);
       if (slot < a.root_cap) {
-        a.roots[slot] = cuboid_root{p, q, t0, t1};
+        a.roots[slot] = cuboid_root{p32, q32, t0, t1};
         a.root_range[slot] = a.surv_range ? a.surv_range[idx] : 0u;
       } else {
         atomicOr(&a.hdr->status, kStatusRootOverflow);

@@ -514,3 +514,86 @@ def test_diagonal_roots_are_not_cuboids():
     asks for t > p^2), so they never give a cuboid."""
     for k in (1, 2, 7, 1000, 2 ** 31 + 11):
         assert not O.theorem_1_1_holds(k, k, k * k)
+
+
+# ---------------------------------------------------------------- 64-bit ranges (beyond section 6's p_max)
+
+def test_coprime_count_brute_force():
+    """The Moebius count of the q prime to p in [q_lo, q_hi] equals the gcd count."""
+    g = random.Random(11)
+    for _ in range(300):
+        p = g.randrange(1, 20000)
+        a = g.randrange(1, 5000)
+        b = a + g.randrange(-3, 700)
+        assert O.coprime_count(p, a, b) == sum(1 for q in range(a, b + 1) if math.gcd(p, q) == 1)
+
+
+def test_coprime_count_periodic_in_q():
+    """Shifting q by a multiple of p keeps every gcd(p, q): the counts of [a, b] and
+    [a + k p, b + k p] agree, at q near 2^39 too (exact integers, no 64-bit bound)."""
+    for p in (30, 9699690, 72796057, 4294967291):
+        for k in (1, 2 ** 39 // p):
+            assert O.coprime_count(p, 1000, 9000) == O.coprime_count(p, 1000 + k * p, 9000 + k * p)
+
+
+def test_sieve_vectorised_vs_pairwise_above_2_32():
+    """Rows of p beyond the paper's 32-bit limit with q above 2^32 (and rows of q with p
+    near 2^39): the numpy sieve (int64 residues) equals the pure-Python-int pairwise
+    sieve, so no 64-bit intermediate overflows."""
+    primes = W.primes_between(11, 41)
+    T = O.Tables(primes)
+    for rng in [W.rect(72796056, 72796058, 2 ** 32 - 150, 2 ** 32 + 150),
+                W.rect(2 ** 39 - 40, 2 ** 39 + 40, 1, 6),
+                W.rect(2 ** 40 - 30, 2 ** 40 - 1, 2 ** 32 - 4, 2 ** 32 - 1)]:
+        assert O.sieve_range(T, rng) == O.sieve_range_pairwise(T, rng)
+
+
+def test_sieve_outcome_depends_on_residues_only():
+    """Section 2: a coprime pair's first rejecting prime depends only on (p mod r, q mod r)
+    for the listed primes.  With L the product of the primes, (p, q) and (p, q + k L)
+    meet the same first rejecter whenever both are coprime, at q beyond 2^39."""
+    primes = [11, 13, 17, 19]
+    T = O.Tables(primes)
+    L = 11 * 13 * 17 * 19
+    k = (2 ** 39) // L
+    for p in (72796057, 2 ** 31 + 11):
+        for q in range(5000, 5400):
+            q2 = q + k * L
+            if math.gcd(p, q) != 1 or math.gcd(p, q2) != 1:
+                continue
+            first = [next((i for i in T.order if T.bit(i, p, x)), None) for x in (q, q2)]
+            assert first[0] == first[1]
+
+
+def test_diagonal_root_near_2_40():
+    """Q_{k,k}(k^2) = 0 at k near 2^40, and for a prime k the divisor search finds
+    exactly that root (the exact root test of 64-bit ranges meets t near 2^80)."""
+    for k in (2 ** 39 + 1, 2 ** 40 - 87):
+        assert O.q_value(k, k, k * k) == 0
+    k = 2 ** 40 - 87
+    assert _is_prime_mr(k)
+    assert O.integer_roots(k, k) == [k * k]
+
+
+def _is_prime_mr(n):
+    """Miller-Rabin with the first twelve primes as bases (exact below 3.3e24)."""
+    if n < 2:
+        return False
+    small = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37)
+    for b in small:
+        if n % b == 0:
+            return n == b
+    d, s = n - 1, 0
+    while d % 2 == 0:
+        d, s = d // 2, s + 1
+    for b in small:
+        x = pow(b, d, n)
+        if x in (1, n - 1):
+            continue
+        for _ in range(s - 1):
+            x = x * x % n
+            if x == n - 1:
+                break
+        else:
+            return False
+    return True
