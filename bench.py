@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c2", "c4top"],
                     help="c2: the 2^14 triangle (the headline); c4top: the 4097 largest rows of the "
                          "2^20 triangle with 256 primes (the long-row regime, for profiling)")
+    ap.add_argument("--wide-only", action="store_true",
+                    help="run only the 64-bit range leg and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -636,17 +638,19 @@ def region_leg(cb, torch, stream, p_to=154000):
 
 
 def wide_leg(cb, torch, stream, rows=16):
-    """64-bit ranges: the rows p = p_max + 1 .. p_max + 16 just beyond the 32-bit limit of
-    section 6 (p_max = 72796055), every q of Eq. 1.2 (q up to 59 p > 2^32: each row is a
-    32-bit piece and a based piece), the 96 primes 11..541 ascending, through
-    cuboid_sieve_wide; beside it the 16 rows just below p_max (32-bit pieces only) through
-    the same call.  Device time (CUDA events around the enqueue, copies back included) and
-    pairs/s; each row's counts and survivors must add up to its pair total."""
+    """64-bit ranges: 16 rows of the region of Eq. 1.2 (every q from q_lo(p) to 59 p) with
+    the 96 primes 11..541 ascending, through cuboid_sieve_wide: the rows from p = 10^8
+    (q up to 5.9 10^9: per row a 32-bit piece of 4.3 10^9 q and a based piece of 1.6 10^9),
+    the rows p_max + 1 .. p_max + 16 just beyond the 32-bit limit of section 6 (p_max =
+    72796055; the based pieces hold a few q), and the 16 rows just below p_max (32-bit
+    pieces only) through the same call.  Device time (CUDA events around the enqueue,
+    copies back included) and pairs/s; each row's counts and survivors must add up to its
+    pair total."""
     p_max = 72796055
     primes = W.primes_between(11, 541)
     t = cb.cuboid_tables_build(primes, cb.ORDER_AS_GIVEN, stream)
     out = {}
-    for name, p0 in (("beyond_p_max", p_max + 1), ("below_p_max", p_max - rows + 1)):
+    for name, p0 in (("rows_from_1e8", 10 ** 8), ("beyond_p_max", p_max + 1), ("below_p_max", p_max - rows + 1)):
         rngs = [W.rect(p, p, cb.cuboid_region_qmin(p), 59 * p) for p in range(p0, p0 + rows)]
         for it in range(3):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -671,6 +675,12 @@ def wide_leg(cb, torch, stream, rows=16):
 
 def main():
     args = parse()
+    if args.wide_only:
+        import torch
+        import paper_1601_00636_gb300 as cb
+        torch.cuda.set_device(0)
+        print(json.dumps({"wide_64bit": wide_leg(cb, torch, torch.cuda.current_stream())}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
