@@ -434,6 +434,7 @@ def run_ours(args):
         line["serving"] = serving_leg(cb, torch, stream)
         line["region_section6"] = region_leg(cb, torch, stream)
         line["wide_64bit"] = wide_leg(cb, torch, stream)
+        line["deep_primes"] = deep_leg(cb, torch, stream)
         line["cpu_baseline"] = cpu_baseline()
     elif rank == 0:
         line["e2e"] = None
@@ -635,6 +636,48 @@ def region_leg(cb, torch, stream, p_to=154000):
             "wall_s": wall, "pairs_per_s": rep["pairs"] / wall, "n_surv": rep["n_surv"],
             "depth": rep["depth"], "r_max": rep["r_max"],
             "paper": "4130 min on its machine for the same rows (section 6; context only)"}
+
+
+def deep_leg(cb, torch, stream, reps=5):
+    """Every prime below the bound of Eq. 2.7 (the 1192 primes from 11 to 9689; 4.4 GB of
+    window rows, far more than the 129 MB L2): table build time and device bytes, then the
+    2^14 triangle sieved with them (plain single-range runs, device time per run with CUDA
+    events around the sieve and root test) in ascending order (the paper's) and in
+    rejection-rate order, beside the 64-prime headline on the same triangle."""
+    primes = W.primes_between(11, 9696)
+    rng = W.c2()["ranges"][0]
+    out = {"primes": f"11..9689 ({len(primes)})", "workload": "triangle 1 <= q < p <= 16384"}
+    for name, flag in (("ascending", cb.ORDER_AS_GIVEN), ("rate", cb.ORDER_BY_RATE)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t = cb.cuboid_tables_build(primes, flag, stream)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        n, dev_bytes, _ = cb.cuboid_tables_info(t)
+        order = cb.cuboid_tables_order(t)
+        res = cb.cuboid_result_create(t, 1)
+        times = []
+        for i in range(reps + 2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                cb.cuboid_sieve_into(res, [rng], cb.MODE_PLAIN, stream)
+                b.record(stream)
+            cb.cuboid_result_wait(res)
+            if i >= 2:
+                times.append(a.elapsed_time(b))
+        got = cb.cuboid_result_get(res, 0, n)
+        cb.cuboid_result_free(res)
+        cb.cuboid_tables_free(t)
+        times.sort()
+        ms = times[len(times) // 2]
+        used = [primes[i] for i, c in enumerate(got["counts"]) if c]
+        out[name] = {"table_bytes": dev_bytes, "table_build_s": build_s, "pairs": got["n_pairs"], "ms": ms,
+                     "pairs_per_s": got["n_pairs"] / (ms / 1e3), "n_surv": len(got["survivors"]),
+                     "first_primes_tried": [primes[i] for i in order[:6]],
+                     "largest_prime_rejecting": max(used) if used else None,
+                     "sums_ok": sum(got["counts"]) + len(got["survivors"]) == got["n_pairs"]}
+    return out
 
 
 def wide_leg(cb, torch, stream, rows=16):

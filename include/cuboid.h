@@ -123,7 +123,8 @@ typedef struct cuboid_stats {
 /* Build the unsolvability tables u_r (Eq. 2.3, Definition 1.1) for n primes on the
  * current device.
  *   primes: host array of n distinct primes, 2 <= r < 9697 (the bound below Eq. 2.7),
- *           1 <= n <= 1024.
+ *           1 <= n <= 1280 (every prime below 9697 fits: the full list from 11 is 1192
+ *           primes, whose tables take 4.4 GB of device memory).
  *   flags:  one CUBOID_ORDER_* | CUBOID_BUILD_*.
  *   stream: work is enqueued on it; the call synchronises the stream before returning
  *           (the effective order is needed on the host).

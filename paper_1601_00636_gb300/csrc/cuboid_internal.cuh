@@ -13,7 +13,7 @@
 
 namespace cuboid {
 
-constexpr uint32_t kMaxPrimes = 1024;
+constexpr uint32_t kMaxPrimes = 1280;       // every prime below the Eq. 2.7 bound (1196 of them) fits
 constexpr uint32_t kPrimeLimit = 9697;     // r < 9697: the bound derived below Eq. 2.7
 constexpr uint32_t kStageSpins = 1u << 22;    // polls of a CTA's staging barrier before it gives up
 constexpr uint32_t kMaxChunkWords = 32768;   // 64-value words per subtile: at most 2^21 pairs

@@ -427,7 +427,7 @@ def test_survivor_overflow_keeps_counts(cb, stream):
 
 def test_status_codes(cb, stream, c1_tables):
     lib = cb._lib
-    for bad in ([4], [11, 11], [9697], [1], [], [2] * 1025):
+    for bad in ([4], [11, 11], [9697], [1], [], [2] * 1025, W.primes_between(11, 10600)):
         with pytest.raises(cb.CuboidError) as e:
             cb.cuboid_tables_build(bad, 0, stream)
         assert e.value.status == cb.EINVAL
@@ -543,6 +543,71 @@ def test_deep_primes_near_eq_2_7_bound(cb, stream):
             _check_against(got, want)
     finally:
         cb.cuboid_tables_free(t)
+
+
+def test_every_prime_below_eq_2_7_bound(cb, stream):
+    """All 1192 primes from 11 to 9689 (every prime the bound below Eq. 2.7 admits), 4.4 GB
+    of window rows.  Ascending order: the table at the highest offset (r = 9689) has the
+    oracle's bits (sampled: the reduced-table lookup and Definition 1.1 pair by pair); the
+    first ten primes' counts and survivors equal the oracle's sieve with those ten, and
+    every survivor of the ten meets the remaining primes in order through Definition 1.1
+    evaluated pair by pair, which fixes the deep counts and the final survivors exactly.
+    Descending order: the deepest primes are tried first, from global memory (no shared-
+    memory prefix holds a 12 MB table); every pair's first rejecter by Definition 1.1."""
+    primes = W.primes_between(11, 9696)
+    assert len(primes) == 1192 and primes[-1] == 9689
+    ranges = [W.rect(100000, 100030, 1, 60000), W.rect(9689 * 3, 9689 * 3 + 2, 9677, 200000)]
+    t = cb.cuboid_tables_build(primes, cb.ORDER_AS_GIVEN, stream)
+    try:
+        n, dev_bytes, _ = cb.cuboid_tables_info(t)
+        assert n == 1192 and dev_bytes > 4 * 10 ** 9
+        r = primes[-1]
+        blob = cb.cuboid_tables_copy_bits(t, len(primes) - 1)
+        assert len(blob) == (r * r + 7) // 8
+        st, got = _run(cb, t, len(primes), ranges, cb.MODE_PLAIN, stream, surv_cap=1 << 20)
+    finally:
+        cb.cuboid_tables_free(t)
+    bit = lambda a, b: (blob[(a * r + b) >> 3] >> ((a * r + b) & 7)) & 1
+    T1 = O.Tables([r], full_limit=0)
+    g = random.Random(7)
+    for _ in range(3000):
+        a, b = g.randrange(r), g.randrange(r)
+        assert bit(a, b) == T1.bit(0, a, b)
+    for _ in range(12):
+        a, b = g.randrange(r), g.randrange(r)
+        assert bit(a, b) == (0 if O.is_solvable(a, b, r) else 1)
+    assert st == cb.OK
+    k = 10
+    T = O.Tables(primes[:k])
+    for res, rng in zip(got, ranges):
+        n_pairs, c_pre, surv_pre = O.sieve_range(T, rng)
+        want = c_pre + [0] * (len(primes) - k)
+        want_surv = []
+        for (p, q) in surv_pre:
+            for i in range(k, len(primes)):
+                if not O.is_solvable(p % primes[i], q % primes[i], primes[i]):
+                    want[i] += 1
+                    break
+            else:
+                want_surv.append((p, q))
+        assert surv_pre and sum(want[k:]) > 0
+        assert res["n_pairs"] == n_pairs and res["counts"] == want
+        assert sorted(res["survivors"]) == sorted(want_surv)
+
+    desc = primes[::-1]
+    rng = W.rect(10 ** 6, 10 ** 6 + 1, 1, 45)
+    t = cb.cuboid_tables_build(desc, cb.ORDER_AS_GIVEN, stream)
+    try:
+        st, (res,) = _run(cb, t, len(desc), [rng], cb.MODE_PLAIN, stream)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert st == cb.OK
+    want = [0] * len(desc)
+    pairs = list(O.pairs_in_range(rng))
+    for (p, q) in pairs:
+        i = next(i for i, rr in enumerate(desc) if not O.is_solvable(p % rr, q % rr, rr))
+        want[i] += 1
+    assert res["n_pairs"] == len(pairs) and res["counts"] == want and res["survivors"] == []
 
 
 def test_staging_wait_gives_up_and_reports(cb, stream, c1_tables):
