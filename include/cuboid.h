@@ -459,6 +459,28 @@ int cuboid_verify_pairs_wide(const uint64_t* p, const uint64_t* q, uint32_t n, v
  * Errors: EINVAL, ERANGE. */
 int cuboid_theorem11_flags_wide(const cuboid_root_wide* roots, uint64_t n, uint8_t* flags);
 
+/* Report of a region scan with 64-bit q (fields as cuboid_search_report). */
+typedef struct cuboid_region_report_wide {
+  uint64_t p, q;      /* where a resumed scan starts: the next row and its first q (0 past 2^32 - 1) */
+  uint32_t r_max;     /* deepest prime needed; 0 if none */
+  uint32_t depth;     /* its 1-based position in the effective order */
+  uint64_t pairs;     /* coprime pairs sieved */
+  uint64_t n_surv;    /* pairs that passed every prime */
+  uint64_t n_roots;   /* integer roots found on them */
+} cuboid_region_report_wide;
+
+/* The synchronous region scan of cuboid_region_scan continued past the paper's p_max
+ * (section 6): rows p_from..p_to of Eq. 1.2 for 1 <= p_from <= p_to < 2^32, row p_from from
+ * q_from on (0: its segment start), every q up to 59 p (which leaves 32 bits for p >
+ * 72796055), sieved as 64-bit ranges with rows of p.  counts: n_primes, caller order (may
+ * be NULL); surv: 2 surv_cap values p0, q0, p1, q1, ... in scan order; roots: root_cap
+ * records; rep: the report.  Synchronous on stream.  Errors: ENOTABLES; ERANGE (p_from = 0,
+ * p_to < p_from, p_to >= 2^32); EQLOW / EQHIGH (q_from outside row p_from's segment);
+ * EOVERFLOW (records past a capacity dropped; counts and totals exact). */
+int cuboid_region_scan_wide(cuboid_tables* t, uint64_t p_from, uint64_t q_from, uint64_t p_to, void* stream,
+                            uint64_t* counts, uint64_t* surv, uint64_t surv_cap, cuboid_root_wide* roots,
+                            uint64_t root_cap, cuboid_region_report_wide* rep);
+
 /* ================================================================ serving */
 
 /* A request loop that admits range queries while others run (continuous batching):

@@ -68,6 +68,11 @@ class cuboid_root_wide(C.Structure):
     _fields_ = [("p", C.c_uint64), ("q", C.c_uint64), ("t_lo", C.c_uint64), ("t_hi", C.c_uint64)]
 
 
+class cuboid_region_report_wide(C.Structure):
+    _fields_ = [("p", C.c_uint64), ("q", C.c_uint64), ("r_max", C.c_uint32), ("depth", C.c_uint32),
+                ("pairs", C.c_uint64), ("n_surv", C.c_uint64), ("n_roots", C.c_uint64)]
+
+
 class cuboid_tuning(C.Structure):
     _fields_ = [("block_threads", C.c_uint32), ("ctas_per_sm", C.c_uint32),
                 ("smem_primes", C.c_uint32), ("tiles_per_warp", C.c_uint32),
@@ -134,6 +139,8 @@ _SIGS = {
     "cuboid_verify_pairs_wide": (C.c_int, [C.POINTER(_u64), C.POINTER(_u64), _u32, _P,
                                            C.POINTER(cuboid_root_wide), _u64, C.POINTER(_u64)]),
     "cuboid_theorem11_flags_wide": (C.c_int, [C.POINTER(cuboid_root_wide), _u64, C.POINTER(C.c_uint8)]),
+    "cuboid_region_scan_wide": (C.c_int, [_P, _u64, _u64, _u64, _P, C.POINTER(_u64), C.POINTER(_u64), _u64,
+                                          C.POINTER(cuboid_root_wide), _u64, C.POINTER(cuboid_region_report_wide)]),
     "cuboid_server_create": (C.c_int, [_P, _u64, _u32, C.POINTER(_P)]),
     "cuboid_server_submit": (C.c_int, [_P, C.POINTER(cuboid_range), C.POINTER(_u64)]),
     "cuboid_server_poll": (C.c_int, [_P, _u64, C.POINTER(_P)]),
@@ -527,6 +534,27 @@ def cuboid_verify_pairs_wide(ps, qs, stream=None, cap: int | None = None):
     _check(_lib.cuboid_verify_pairs_wide(pa, qa, n, _stream(stream), out, cap, C.byref(nr)),
            "cuboid_verify_pairs_wide")
     return [(int(out[i].p), int(out[i].q), (int(out[i].t_hi) << 64) | int(out[i].t_lo)) for i in range(nr.value)]
+
+
+def cuboid_region_scan_wide(t, p_from: int, p_to: int, q_from: int = 0, stream=None,
+                            surv_cap: int = 1 << 16, root_cap: int = 1 << 12):
+    """Scan rows p_from..p_to (< 2^32) of the region with 64-bit q.  Returns (status, report
+    dict, counts in caller order, survivor (p, q) list, root (p, q, t) list); status is OK
+    or EOVERFLOW, others raise."""
+    n = cuboid_tables_info(t)[0]
+    counts = (_u64 * n)()
+    surv = (_u64 * max(2 * surv_cap, 2))()
+    roots = (cuboid_root_wide * max(root_cap, 1))()
+    rep = cuboid_region_report_wide()
+    st = _lib.cuboid_region_scan_wide(t, p_from, q_from, p_to, _stream(stream), counts, surv, surv_cap, roots,
+                                      root_cap, C.byref(rep))
+    if st not in (OK, EOVERFLOW):
+        _check(st, "cuboid_region_scan_wide")
+    d = {k: getattr(rep, k) for k, _ in cuboid_region_report_wide._fields_}
+    ns, nr = min(d["n_surv"], surv_cap), min(d["n_roots"], root_cap)
+    sv = [(int(surv[2 * i]), int(surv[2 * i + 1])) for i in range(ns)]
+    rv = [(int(roots[i].p), int(roots[i].q), (int(roots[i].t_hi) << 64) | int(roots[i].t_lo)) for i in range(nr)]
+    return st, d, list(counts), sv, rv
 
 
 def cuboid_theorem11_flags_wide(roots) -> list[bool]:

@@ -3,7 +3,9 @@
 // upward in batches of 100 rows through the batched sieve (one range per row), with the
 // paper's toolkit: start at (p, q), read the current p and the deepest prime needed per
 // hundred rows, stop with a report that a later start resumes from.  The scan runs on a
-// host thread; the device work is the sieve and root test of the batched path.
+// host thread; the device work is the sieve and root test of the batched path.  Past the
+// paper's p_max (59 p beyond 32 bits) a synchronous scan continues through the 64-bit
+// ranges, rows of p with q cut into pieces below and above 2^32.
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
@@ -23,6 +25,7 @@ int result_create(const cuboid_tables* t, uint32_t max_ranges, uint64_t surv_cap
 int sieve_into(cuboid_result* r, const cuboid_range* ranges, uint32_t n, uint32_t mode, cudaStream_t s,
                bool device_ranges, bool download);
 int result_wait(cuboid_result* r);
+int sieve_wide_into(cuboid_result* r, const cuboid_range_wide* ranges, uint32_t n, cudaStream_t s);
 }  // namespace cuboid
 
 using namespace cuboid;
@@ -208,6 +211,78 @@ extern "C" int cuboid_region_scan(cuboid_tables* t, uint32_t p_from, uint32_t q_
   const uint32_t np = p_to + 1;
   fill_report(t, tot, np, np <= kPMax ? qmin(np) : 0u, rep);
   if (overflow || tot.surv.size() > surv_cap || tot.roots.size() > root_cap) return CUBOID_EOVERFLOW;
+  return CUBOID_OK;
+}
+
+// ------------------------------------------------------------------ past p_max (64-bit q)
+
+extern "C" int cuboid_region_scan_wide(cuboid_tables* t, uint64_t p_from, uint64_t q_from, uint64_t p_to,
+                                       void* stream, uint64_t* counts, uint64_t* surv, uint64_t surv_cap,
+                                       cuboid_root_wide* roots, uint64_t root_cap, cuboid_region_report_wide* rep) {
+  constexpr uint64_t k2p32 = 1ull << 32;
+  if (!t) return CUBOID_ENOTABLES;
+  if (p_from == 0 || p_to < p_from || p_to >= k2p32) return CUBOID_ERANGE;
+  if (q_from != 0 && q_from < qmin((uint32_t)p_from)) return CUBOID_EQLOW;
+  if (q_from > 59ull * p_from) return CUBOID_EQHIGH;
+  cudaStream_t s = (cudaStream_t)stream;
+  // pieces of one row: the q below 2^32, then at most 2^32 - 64 q a piece
+  const uint64_t top = 59ull * p_to;
+  const uint64_t per_row = 1 + (top >= k2p32 ? (top - k2p32) / (k2p32 - 64) + 1 : 0);
+  cuboid_result* res = nullptr;
+  int st = result_create(t, (uint32_t)(kBatchRows * per_row), 1ull << 16, 1ull << 12, &res);
+  if (st != CUBOID_OK) return st;
+  Totals tot;
+  tot.counts.assign(t->n, 0);
+  std::vector<uint64_t> c(t->n), sv;
+  std::vector<cuboid_root_wide> rv;
+  std::vector<cuboid_range_wide> rg;
+  bool overflow = false;
+  for (uint64_t p = p_from; p <= p_to && st == CUBOID_OK;) {
+    const uint64_t e = std::min<uint64_t>(p_to, p / kBatchRows * kBatchRows + kBatchRows - 1);
+    rg.clear();
+    for (uint64_t x = p; x <= e; ++x) {
+      const uint64_t lo = x == p_from ? std::max<uint64_t>(q_from, qmin((uint32_t)x)) : qmin((uint32_t)x);
+      if (lo <= 59ull * x) rg.push_back(cuboid_range_wide{x, x, lo, 59ull * x, CUBOID_ROWS_P, 0u});
+    }
+    p = e + 1;
+    if (rg.empty()) continue;
+    st = sieve_wide_into(res, rg.data(), (uint32_t)rg.size(), s);
+    if (st != CUBOID_OK) break;
+    st = result_wait(res);
+    if (st == CUBOID_EOVERFLOW) {
+      overflow = true;
+      st = CUBOID_OK;
+    }
+    for (uint32_t k = 0; k < rg.size() && st == CUBOID_OK; ++k) {
+      uint64_t np = 0, ns = 0, nr = 0;
+      const uint64_t* sp = nullptr;
+      const cuboid_root_wide* rp = nullptr;
+      st = cuboid_result_get_wide(res, k, &np, c.data(), &ns, &sp, &nr, &rp);
+      for (uint32_t i = 0; i < t->n; ++i) tot.counts[i] += c[i];
+      tot.pairs += np;
+      tot.n_surv += ns;
+      tot.n_roots += nr;
+      sv.insert(sv.end(), sp, sp + 2 * ns);
+      rv.insert(rv.end(), rp, rp + nr);
+    }
+  }
+  result_wait(res);
+  cuboid_result_free(res);
+  if (st != CUBOID_OK) return st;
+  if (counts) std::memcpy(counts, tot.counts.data(), t->n * sizeof(uint64_t));
+  if (surv) std::memcpy(surv, sv.data(), std::min<uint64_t>(2 * surv_cap, sv.size()) * sizeof(uint64_t));
+  if (roots) std::memcpy(roots, rv.data(), std::min<uint64_t>(root_cap, rv.size()) * sizeof(cuboid_root_wide));
+  if (rep) {
+    cuboid_region_report_wide r{};
+    r.p = p_to + 1;
+    r.q = p_to + 1 < k2p32 ? qmin((uint32_t)(p_to + 1)) : 0;
+    deepest(t, tot.counts, tot.n_surv, &r.depth, &r.r_max);
+    r.pairs = tot.pairs;
+    r.n_surv = tot.n_surv;
+    r.n_roots = tot.n_roots;
+    *rep = r;
+  }
+  if (overflow || sv.size() > 2 * surv_cap || rv.size() > root_cap) return CUBOID_EOVERFLOW;
   return CUBOID_OK;
 }
 

@@ -756,10 +756,13 @@ extern "C" int cuboid_wide_pieces(const cuboid_range_wide* r, cuboid_range* piec
   return CUBOID_OK;
 }
 
-extern "C" int cuboid_sieve_wide(const cuboid_tables* t, const cuboid_range_wide* ranges, uint32_t n, void* stream,
-                                 cuboid_result** out) {
-  if (!t) return CUBOID_ENOTABLES;
-  if (!out || !ranges || n == 0) return CUBOID_EINVAL;
+namespace cuboid {
+
+// Sieve n 64-bit ranges on an existing result object (enough ranges for their pieces),
+// enqueued on s with the copies back.  ETOOLARGE: more pieces than r holds.
+int sieve_wide_into(cuboid_result* r, const cuboid_range_wide* ranges, uint32_t n, cudaStream_t s) {
+  if (!r || !r->t || r->host_only || !ranges || n == 0) return CUBOID_EINVAL;
+  if (check_device(r) != CUBOID_OK) return CUBOID_EINVAL;
   std::vector<cuboid_range> pieces;
   std::vector<unsigned long long> bases;
   std::vector<uint32_t> owner;
@@ -769,31 +772,53 @@ extern "C" int cuboid_sieve_wide(const cuboid_tables* t, const cuboid_range_wide
     if (st != CUBOID_OK) return st;
     owner.insert(owner.end(), pieces.size() - before, i);
   }
-  if (pieces.size() >= 0xFFFFFFFFull) return CUBOID_ETOOLARGE;
-  int dev = -1;
-  cudaGetDevice(&dev);
-  if (dev != t->device) return CUBOID_EINVAL;
-  cuboid_result* r = nullptr;
-  int st = result_create(t, std::max<uint32_t>((uint32_t)pieces.size(), 1u), 0, 0, &r);
-  if (st != CUBOID_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
+  if (pieces.size() > r->max_ranges) return CUBOID_ETOOLARGE;
+  cudaError_t e = cudaSuccess;
   const size_t nb = std::max<size_t>(bases.size(), 2);
-  cudaError_t e = cudaMalloc(&r->d_base, nb * sizeof(unsigned long long));
-  if (e == cudaSuccess) {
+  if (r->d_base_cap < nb) {
+    cudaFree(r->d_base);
+    r->d_base = nullptr;
+    r->d_base_cap = 0;
+    e = cudaMalloc(&r->d_base, nb * sizeof(unsigned long long));
+    if (e != cudaSuccess) return status_from_cuda(e);
     r->d_base_cap = nb;
-    if (!bases.empty())
-      e = cudaMemcpyAsync(r->d_base, bases.data(), bases.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
-                          s);
   }
+  cudaEventSynchronize(r->done);  // h_base may still feed the copy of an earlier run
   r->wide = true;
   r->n_wide = n;
   r->piece_of = owner;
   r->h_base = bases;
+  if (!bases.empty())
+    e = cudaMemcpyAsync(r->d_base, r->h_base.data(), bases.size() * sizeof(unsigned long long),
+                        cudaMemcpyHostToDevice, s);
   r->n_ranges = (uint32_t)pieces.size();
   r->downloaded = false;
   r->fetched = false;
   if (e == cudaSuccess) e = run_kernels_wide(r, pieces, s);
-  st = e == cudaSuccess ? enqueue_download(r, s) : status_from_cuda(e);
+  return e == cudaSuccess ? enqueue_download(r, s) : status_from_cuda(e);
+}
+
+}  // namespace cuboid
+
+extern "C" int cuboid_sieve_wide(const cuboid_tables* t, const cuboid_range_wide* ranges, uint32_t n, void* stream,
+                                 cuboid_result** out) {
+  if (!t) return CUBOID_ENOTABLES;
+  if (!out || !ranges || n == 0) return CUBOID_EINVAL;
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    uint32_t k = 0;
+    const int st = cuboid_wide_pieces(&ranges[i], nullptr, nullptr, 0, &k);
+    if (st != CUBOID_OK && st != CUBOID_EOVERFLOW) return st;
+    total += k;
+  }
+  if (total >= 0xFFFFFFFFull) return CUBOID_ETOOLARGE;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return CUBOID_EINVAL;
+  cuboid_result* r = nullptr;
+  int st = result_create(t, std::max<uint32_t>((uint32_t)total, 1u), 0, 0, &r);
+  if (st != CUBOID_OK) return st;
+  st = sieve_wide_into(r, ranges, n, (cudaStream_t)stream);
   if (st != CUBOID_OK) {
     result_release(r);
     return st;

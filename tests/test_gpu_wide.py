@@ -205,3 +205,71 @@ def test_verify_pairs_wide_matches_oracle(cb, stream):
     with pytest.raises(cb.CuboidError) as e:
         cb.cuboid_verify_pairs_wide([1 << 40], [3], stream=stream)
     assert e.value.status == cb.ERANGE
+
+
+# ---------------------------------------------------------------- the region scan past p_max
+
+def test_region_scan_wide_equals_32bit_scan(cb, stream):
+    """Below p_max the 64-bit scan equals the 32-bit scan of section 5 (itself checked
+    against the oracle's region scan): rows 140..400 across the switch of Eq. 5.1 to
+    Eq. 5.2, and the last six rows below p_max whose q reach 2^32 - 1."""
+    primes = W.primes_between(11, 61)
+    t = cb.cuboid_tables_build(primes, cb.ORDER_AS_GIVEN)
+    try:
+        for p_from, q_from, p_to in [(140, 0, 400), (P_MAX - 5, 0, P_MAX), (250, 14000, 260)]:
+            a = cb.cuboid_region_scan(t, p_from, p_to, q_from=q_from, stream=stream)
+            b = cb.cuboid_region_scan_wide(t, p_from, p_to, q_from=q_from, stream=stream)
+            assert a[0] == b[0] == cb.OK
+            assert a[2] == b[2] and a[3] == b[3] and a[4] == b[4]
+            for k in ("pairs", "n_surv", "n_roots", "depth", "r_max", "p"):
+                assert a[1][k] == b[1][k], k
+            # the 32-bit scan cannot resume past p_max and reports q = 0 there
+            assert b[1]["q"] == O.region_q_bounds(p_to + 1)[0]
+            assert a[1]["q"] == (b[1]["q"] if p_to < P_MAX else 0)
+    finally:
+        cb.cuboid_tables_free(t)
+
+
+def test_region_scan_wide_past_p_max(cb, stream):
+    """Rows p_max - 3 .. p_max + 4 with the 96 primes 11..541 ascending (section 6's list):
+    the pair total is the oracle's Moebius count of every row's segment of Eq. 1.2, counts
+    and survivors add up to it, depth and r_max follow from the counts as the oracle reads
+    them, the report points at the next row's first q, the counts equal those of the same
+    rows through cuboid_sieve_wide, and a scan stopped at p_max and resumed from the report
+    adds up to the whole."""
+    primes = W.primes_between(11, 541)
+    T = O.Tables(primes, full_limit=0)
+    a, b = P_MAX - 3, P_MAX + 4
+    t = cb.cuboid_tables_build(primes, cb.ORDER_AS_GIVEN)
+    try:
+        st, rep, counts, surv, roots = cb.cuboid_region_scan_wide(t, a, b, stream=stream)
+        rows = [W.rect(p, p, O.region_q_bounds(p)[0], O.region_q_bounds(p)[1]) for p in range(a, b + 1)]
+        st_w, got = _run(cb, t, rows, len(primes), stream)
+        st1, rep1, c1, s1, r1 = cb.cuboid_region_scan_wide(t, a, P_MAX, stream=stream)
+        st2, rep2, c2, s2, r2 = cb.cuboid_region_scan_wide(t, rep1["p"], b, q_from=rep1["q"], stream=stream)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert st == st_w == st1 == st2 == cb.OK
+    want_pairs = sum(O.coprime_count(p, *O.region_q_bounds(p)) for p in range(a, b + 1))
+    assert rep["pairs"] == want_pairs == sum(g["n_pairs"] for g in got)
+    assert sum(counts) + rep["n_surv"] == rep["pairs"]
+    assert counts == [sum(c) for c in zip(*[g["counts"] for g in got])]
+    assert sorted(surv) == sorted(s for g in got for s in g["survivors"]) and roots == []
+    assert (rep["depth"], rep["r_max"]) == O.deepest_prime(T, counts, rep["n_surv"])
+    assert (rep["p"], rep["q"]) == (b + 1, O.region_q_bounds(b + 1)[0])
+    assert (rep1["p"], rep1["q"]) == (P_MAX + 1, O.region_q_bounds(P_MAX + 1)[0])
+    assert [x + y for x, y in zip(c1, c2)] == counts and rep1["pairs"] + rep2["pairs"] == rep["pairs"]
+    assert rows[-1]["q_hi"] > TWO32 > rows[0]["q_hi"]
+
+
+def test_region_scan_wide_errors(cb, stream):
+    t = cb.cuboid_tables_build(W.primes_between(11, 31), cb.ORDER_AS_GIVEN)
+    try:
+        for args, kw, code in [((0, 5), {}, cb.ERANGE), ((10, 9), {}, cb.ERANGE), ((5, TWO32), {}, cb.ERANGE),
+                               ((P_MAX + 10, P_MAX + 11), {"q_from": 3}, cb.EQLOW),
+                               ((P_MAX + 10, P_MAX + 11), {"q_from": 59 * (P_MAX + 10) + 1}, cb.EQHIGH)]:
+            with pytest.raises(cb.CuboidError) as e:
+                cb.cuboid_region_scan_wide(t, *args, stream=stream, **kw)
+            assert e.value.status == code
+    finally:
+        cb.cuboid_tables_free(t)
