@@ -53,6 +53,8 @@ def parse():
                          "2^20 triangle with 256 primes (the long-row regime, for profiling)")
     ap.add_argument("--wide-only", action="store_true",
                     help="run only the 64-bit range leg and print its JSON (for profiling)")
+    ap.add_argument("--root-only", action="store_true",
+                    help="run only the bulk root-test leg and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -435,6 +437,7 @@ def run_ours(args):
         line["region_section6"] = region_leg(cb, torch, stream)
         line["wide_64bit"] = wide_leg(cb, torch, stream)
         line["deep_primes"] = deep_leg(cb, torch, stream)
+        line["root_test"] = root_test_leg(cb, torch, stream)
         line["cpu_baseline"] = cpu_baseline()
     elif rank == 0:
         line["e2e"] = None
@@ -638,6 +641,39 @@ def region_leg(cb, torch, stream, p_to=154000):
             "paper": "4130 min on its machine for the same rows (section 6; context only)"}
 
 
+def root_test_leg(cb, torch, stream, n_max=1024, reps=3):
+    """The exact root test in bulk: the tables of 3, 5 and 7 are all zero (section 2), so
+    every coprime pair of the triangle 1 <= q < p <= 1024 survives the sieve and goes
+    through the root test.  CUDA events around the whole run (sieve, root test, copies)
+    and around the sieve launch alone (CUBOID_MODE_TIME_SIEVE); the root test's share is
+    the difference."""
+    t = cb.cuboid_tables_build([3, 5, 7], cb.ORDER_AS_GIVEN, stream)
+    res = cb.cuboid_result_create(t, 1, 1 << 20, 1 << 12)
+    rng = W.triangle(n_max)
+    runs = []
+    for i in range(reps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            cb.cuboid_sieve_into(res, [rng], cb.MODE_PLAIN | cb.MODE_TIME_SIEVE, stream)
+            b.record(stream)
+        st = cb.cuboid_result_wait(res)
+        sieve_ms, _ = cb.cuboid_result_sieve_ms(res)
+        if i:
+            runs.append((a.elapsed_time(b), sieve_ms))
+    got = cb.cuboid_result_get(res, 0, 3)
+    cb.cuboid_result_free(res)
+    cb.cuboid_tables_free(t)
+    runs.sort()
+    total, sieve = runs[len(runs) // 2]
+    n = len(got["survivors"])
+    return {"workload": f"triangle 1 <= q < p <= {n_max}, primes 3, 5, 7 (every coprime pair survives)",
+            "status": st, "survivors": n, "roots": len(got["roots"]), "ms_total": total, "ms_sieve": sieve,
+            "ms_root_test": total - sieve, "survivors_per_s": n / ((total - sieve) / 1e3),
+            "thread_us_per_survivor": (total - sieve) * 1e3 / max(n, 1) * (cb.cuboid_device_sms() * 2 * 64),
+            "note": "root-test grid: 2 CTAs of 64 threads per SM; thread-us per survivor = root-test time x threads / survivors"}
+
+
 def deep_leg(cb, torch, stream, reps=5):
     """Every prime below the bound of Eq. 2.7 (the 1192 primes from 11 to 9689; 4.4 GB of
     window rows, far more than the 129 MB L2): table build time and device bytes, then the
@@ -723,6 +759,12 @@ def main():
         import paper_1601_00636_gb300 as cb
         torch.cuda.set_device(0)
         print(json.dumps({"wide_64bit": wide_leg(cb, torch, torch.cuda.current_stream())}), flush=True)
+        return
+    if args.root_only:
+        import torch
+        import paper_1601_00636_gb300 as cb
+        torch.cuda.set_device(0)
+        print(json.dumps({"root_test": root_test_leg(cb, torch, torch.cuda.current_stream())}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
