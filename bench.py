@@ -670,8 +670,8 @@ def root_test_leg(cb, torch, stream, n_max=1024, reps=3):
     return {"workload": f"triangle 1 <= q < p <= {n_max}, primes 3, 5, 7 (every coprime pair survives)",
             "status": st, "survivors": n, "roots": len(got["roots"]), "ms_total": total, "ms_sieve": sieve,
             "ms_root_test": total - sieve, "survivors_per_s": n / ((total - sieve) / 1e3),
-            "thread_us_per_survivor": (total - sieve) * 1e3 / max(n, 1) * (cb.cuboid_device_sms() * 2 * 64),
-            "note": "root-test grid: 2 CTAs of 64 threads per SM; thread-us per survivor = root-test time x threads / survivors"}
+            "thread_us_per_survivor": (total - sieve) * 1e3 / max(n, 1) * (cb.cuboid_device_sms() * 2 * 256),
+            "note": "root-test grid: 2 CTAs of 256 threads per SM; thread-us per survivor = root-test time x threads / survivors"}
 
 
 def deep_leg(cb, torch, stream, reps=5):
