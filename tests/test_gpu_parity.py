@@ -175,7 +175,7 @@ def test_c1_parity(cb, stream, mode, dens):
     assert got[0]["n_pairs"] == 12231
 
 
-def test_c1_north_star_call(cb, stream, c1_tables):
+def test_c1_single_range_call(cb, stream, c1_tables):
     """cuboid_sieve(p_lo, p_hi, q_lo, q_hi) as the paper states the problem."""
     res = cb.cuboid_sieve(c1_tables, 2, 200, 1, 199, cb.Q_LT_P, stream)
     assert cb.cuboid_result_wait(res) == cb.OK
