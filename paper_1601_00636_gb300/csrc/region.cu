@@ -41,7 +41,7 @@ constexpr uint32_t kFirstSearchP = 152;  // Eq. 5.2 holds from here on (section 
 uint32_t qmin(uint32_t p) {
   uint64_t q1 = 1;
   while (9 * q1 * q1 * q1 < p) ++q1;
-  const uint64_t q2 = (p + 58) / 59;
+  const uint64_t q2 = ((uint64_t)p + 58) / 59;  // p + 58 may pass 2^32
   uint64_t q = std::min(q1, q2);
   return (uint32_t)std::max<uint64_t>(q, 1);
 }

@@ -16,6 +16,18 @@ def test_region_qmin_matches_oracle():
         assert cb.cuboid_region_qmin(p) == O.region_q_bounds(p)[0]
 
 
+def test_region_qmin_past_p_max():
+    """Rows the 64-bit region scan visits: p_max + 1 up to 2^32 - 1, including the values
+    where ceil((p / 9)^(1/3)) steps (9 q^3 = p and its neighbours)."""
+    cb = _cb()
+    ps = [72796056, 72796057, 10 ** 8, 2 ** 31, 2 ** 32 - 2, 2 ** 32 - 1]
+    for q in (200, 201, 500, 777, 780, 781):
+        ps += [9 * q ** 3 - 1, 9 * q ** 3, 9 * q ** 3 + 1]
+    for p in ps:
+        if p < 2 ** 32:
+            assert cb.cuboid_region_qmin(p) == O.region_q_bounds(p)[0], p
+
+
 def test_report_file_format(tmp_path):
     """Section 5's report: a time stamp line, then the exit values of p, q and r_max."""
     cb = _cb()
