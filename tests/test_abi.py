@@ -59,3 +59,42 @@ def test_null_handles_are_rejected(lib_path):
     assert lib.cuboid_sieve(None, 1, 2, 1, 2, 0, None, None) == cb.ENOTABLES
     assert lib.cuboid_server_destroy(None, 0) == cb.EINVAL
     assert lib.cuboid_probe_int_issue(5, 1, 32, 1, None, None) == cb.EINVAL
+    assert lib.cuboid_sieve_wide(None, None, 0, None, None) == cb.ENOTABLES
+    assert lib.cuboid_result_get_wide(None, 0, None, None, None, None, None, None) == cb.EINVAL
+    assert lib.cuboid_region_scan_wide(None, 1, 0, 2, None, None, None, 0, None, 0, None) == cb.ENOTABLES
+    assert lib.cuboid_verify_pairs_wide(None, None, 0, None, None, 0, None) == cb.EINVAL
+    assert lib.cuboid_wide_pieces(None, None, None, 0, None) == cb.EINVAL
+
+
+_STRUCTS = {
+    "cuboid_range": ["p_lo", "p_hi", "q_lo", "q_hi", "flags", "reserved"],
+    "cuboid_root": ["p", "q", "t_lo", "t_hi"],
+    "cuboid_tuning": ["block_threads", "ctas_per_sm", "smem_primes", "tiles_per_warp", "hot_primes", "row_lanes"],
+    "cuboid_stats": ["words", "word_steps", "warp_steps", "tiles"],
+    "cuboid_search_report": ["p", "q", "r_max", "depth", "pairs", "n_surv", "n_roots"],
+    "cuboid_range_wide": ["p_lo", "p_hi", "q_lo", "q_hi", "flags", "reserved"],
+    "cuboid_root_wide": ["p", "q", "t_lo", "t_hi"],
+    "cuboid_region_report_wide": ["p", "q", "r_max", "depth", "pairs", "n_surv", "n_roots"],
+}
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every struct of include/cuboid.h has the same size and field offsets in C (gcc on
+    the header) as in the ctypes binding."""
+    import paper_1601_00636_gb300 as cb
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cuboid.h"', "int main(void) {"]
+    for name, fields in _STRUCTS.items():
+        offs = " ".join("%zu" for _ in fields)
+        args = ", ".join(f"offsetof({name}, {f})" for f in fields)
+        lines.append(f'  printf("{name} %zu {offs}\\n", sizeof({name}), {args});')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    for ln in out.splitlines():
+        name, size, *offs = ln.split()
+        st = getattr(cb, name)
+        assert ctypes.sizeof(st) == int(size), name
+        assert [getattr(st, f).offset for f in _STRUCTS[name]] == [int(o) for o in offs], name
