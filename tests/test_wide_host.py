@@ -134,3 +134,15 @@ def test_theorem11_wide_matches_oracle(cb):
     assert any(flags) and not all(flags)
     with pytest.raises(cb.CuboidError):
         cb.cuboid_theorem11_flags_wide([(1 << 40, 1, 5)])
+
+
+def test_device_root_bound_covers_oracle_bound():
+    """The root test isolates the roots of R(u) = Q(sqrt u) in [0, 45 M^4], M = max(p, q);
+    for pairs up to 2^40 (64-bit ranges) that interval holds the oracle's bound on every
+    positive root, and 45 M^4 stays below the 2^166 the device's three 64-bit limbs use."""
+    g = random.Random(17)
+    cases = [(1, 1), (2, 1), (1, 2), ((1 << 40) - 1, 1), (1, (1 << 40) - 1), ((1 << 40) - 1, (1 << 40) - 1)]
+    cases += [(g.randrange(1, 1 << 40), g.randrange(1, 1 << 40)) for _ in range(300)]
+    for p, q in cases:
+        M = max(p, q)
+        assert O.root_bound_u(p, q) <= 45 * M ** 4 < 1 << 166
