@@ -193,6 +193,71 @@ def test_unsolvable_counts_brute_force():
         assert O.unsolvable_count(r) == brute
 
 
+# Number of k in [0, r) with v_r(k) = u_r(k, 1) = 1 for the first 24 odd primes.  The values
+# for r = 11..41 are the survey's independent scratch computation; all 24 were recomputed
+# by sympy's polynomial factorisation over GF(r) (a linear factor of Q_{k,1}(t) mod r means
+# a root), a method that shares nothing with the oracle's evaluation at every t~.
+UNSOLVABLE_K = {3: 0, 5: 0, 7: 0, 11: 8, 13: 4, 17: 12, 19: 12, 23: 16, 29: 20, 31: 16, 37: 24,
+                41: 28, 43: 24, 47: 24, 53: 40, 59: 32, 61: 36, 67: 28, 71: 40, 73: 56, 79: 32,
+                83: 48, 89: 44, 97: 64}
+
+# Those counts ranked by hand: decreasing count / r (density) and count / (r + 1) (rate),
+# ties to the smaller r.  For these 24 primes both rankings agree.
+ORDER_24 = [73, 53, 11, 17, 23, 29, 41, 97, 37, 19, 61, 83, 71, 43, 59, 31, 47, 89, 67, 79, 13, 3, 5, 7]
+
+# The 1 <= q < p <= 200 triangle with the first 24 odd primes in ascending order (the
+# paper's order, section 2): the survey's independent scratch computation of the pair
+# total, the survivors and each prime's first-rejecter count (every prime not listed: 0).
+C1_PAIRS = 12231
+C1_COUNTS = {11: 8153, 13: 1164, 17: 1940, 19: 612, 23: 255, 29: 75, 31: 19, 37: 8, 41: 3, 43: 2}
+
+
+def test_unsolvable_counts_literal():
+    """Definition 1.1 at (k, 1) for every k: the oracle's counts equal the literals."""
+    for r, want in UNSOLVABLE_K.items():
+        assert O.unsolvable_count(r) == want, r
+
+
+@pytest.mark.parametrize("r", [43, 53, 73, 97])
+def test_unsolvable_literals_by_factorisation(r):
+    """The literals themselves, recomputed here by factoring Q_{k,1}(t) over GF(r) with
+    sympy (a root mod r is a linear factor; the zero polynomial is solvable)."""
+    sp = pytest.importorskip("sympy")
+    t = sp.symbols("t")
+    n = 0
+    for k in range(r):
+        c = O.q_coefficients(k, 1)
+        poly = sp.Poly(sum(v * t ** e for e, v in c.items()), t, modulus=r)
+        solv = poly.is_zero or any(f.degree() == 1 for f, _ in poly.factor_list()[1])
+        n += 0 if solv else 1
+    assert n == UNSOLVABLE_K[r]
+
+
+@pytest.mark.parametrize("mode", [True, "rate"])
+def test_effective_order_literal(mode):
+    """The density and rate orders of the first 24 odd primes equal the hand ranking."""
+    primes = W.first_odd_primes(24)
+    T = O.Tables(primes, mode, full_limit=0)
+    assert [primes[i] for i in T.order] == ORDER_24
+
+
+@pytest.mark.parametrize("pairwise", [False, True])
+def test_c1_literal_counts(pairwise):
+    """Section 2 sieve, section 5 loop: C1 in ascending order against the literal pair
+    total, survivors and first-rejecter counts.  A wrong first rejecter, an off-by-one at
+    q < p or a leaked diagonal pair changes one of them."""
+    primes = W.first_odd_primes(24)
+    res = O.run(primes, [W.triangle(200)], pairwise=pairwise)["ranges"][0]
+    assert res["n_pairs"] == C1_PAIRS
+    assert res["survivors"] == [] and res["roots"] == []
+    assert res["counts"] == [C1_COUNTS.get(r, 0) for r in primes]
+
+
+def test_c1_literal_counts_by_totient():
+    """The C1 pair total is sum_{p=2..200} phi(p), a closed count."""
+    assert int(_phi_sum(200)[2:].sum()) == C1_PAIRS
+
+
 def test_effective_order_by_density():
     primes = W.first_odd_primes(40)
     cnt = [O.unsolvable_count(r) for r in primes]
