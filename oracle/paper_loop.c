@@ -138,107 +138,173 @@ static uint32_t factors(uint32_t x, uint32_t* f) {
   return n;
 }
 
-/* Sieves the rows p_lo..p_hi of the range [p_lo, p_hi] x [q_lo, q_hi] (flags: 1 = q < p),
- * trying the primes in the order order[0..n-1] (indices into the build list).
- * counts[n] (build-list order) and *n_pairs are ADDED to; survivors (p << 32 | q) are
- * written up to surv_cap (unsorted) and *n_surv is ADDED the number of them all.  threads <= 0: OpenMP's default.
+/* One range of a sieve call: inclusive bounds, flags 1 = q < p. */
+typedef struct {
+  uint32_t p_lo, p_hi, q_lo, q_hi, flags;
+} pl_range;
+
+/* Per-thread scratch of the row loop. */
+typedef struct {
+  uint32_t* pr;          /* (p mod r) r per prime, effective order */
+  const uint8_t** tab;   /* tables, effective order */
+  uint32_t* rr;          /* primes, effective order */
+  uint8_t* shared;       /* q sharing a prime factor with p (or q = p), per row */
+  size_t shared_cap;
+} pl_scratch;
+
+/* Row p of range R: every coprime q != p tries the primes in order; the first prime whose
+ * bit is set takes the pair's count (cnt, effective order); survivors go to surv at slots
+ * taken from *surv_pos.  Returns the pairs sieved, or -1 when out of memory. */
+static int64_t sieve_row(const pl_range* R, uint32_t p, uint32_t n, pl_scratch* S, uint64_t* cnt,
+                         uint64_t* n_surv, uint64_t* surv, uint32_t* surv_range, uint32_t range_idx,
+                         uint64_t surv_cap, uint64_t* surv_pos) {
+  uint32_t hi = R->q_hi;
+  if ((R->flags & 1u) && (uint64_t)hi >= p) hi = p - 1;
+  if (hi < R->q_lo) return 0;
+  const uint32_t lo = R->q_lo;
+  const size_t len = (size_t)hi - lo + 1;
+  if (len > S->shared_cap) {
+    free(S->shared);
+    S->shared = (uint8_t*)malloc(len);
+    S->shared_cap = S->shared ? len : 0;
+    if (!S->shared) return -1;
+  }
+  uint8_t* shared = S->shared;
+  memset(shared, 0, len);
+  uint32_t f[10];
+  const uint32_t nf = factors(p, f);
+  for (uint32_t j = 0; j < nf; ++j) {
+    const uint64_t first = ((uint64_t)lo + f[j] - 1) / f[j] * f[j];
+    for (uint64_t m = first; m <= hi; m += f[j]) shared[m - lo] = 1;
+  }
+  if (p >= lo && p <= hi) shared[p - lo] = 1;  /* p != q */
+  for (uint32_t e = 0; e < n; ++e) S->pr[e] = (p % S->rr[e]) * S->rr[e];
+  int64_t pairs = 0;
+  for (uint64_t q = lo; q <= hi; ++q) {
+    if (shared[q - lo]) continue;
+    ++pairs;
+    uint32_t e = 0;
+    for (; e < n; ++e) {  /* the first prime whose bit is set rejects the pair */
+      const uint32_t idx = S->pr[e] + (uint32_t)q % S->rr[e];
+      if ((S->tab[e][idx >> 3] >> (idx & 7)) & 1u) break;
+    }
+    if (e < n) {
+      ++cnt[e];
+    } else {
+      ++*n_surv;
+      if (surv) {
+        uint64_t pos;
+#pragma omp atomic capture
+        pos = (*surv_pos)++;
+        if (pos < surv_cap) {
+          surv[pos] = ((uint64_t)p << 32) | q;
+          if (surv_range) surv_range[pos] = range_idx;
+        }
+      }
+    }
+  }
+  return pairs;
+}
+
+/* Sieves n_ranges ranges, trying the primes in the order order[0..n-1] (indices into the
+ * build list); the rows of all ranges are the work items (largest row first within a
+ * range).  counts[k * n + i] (build-list order) and n_pairs[k] are ADDED to; survivors
+ * (p << 32 | q, unsorted) and their range index are written up to surv_cap, and *n_surv
+ * is ADDED the number of them all.  threads <= 0: OpenMP's default.
  * Returns 0, or -1 on bad arguments, -2 when out of memory. */
-int pl_sieve(const pl_tables* T, const uint32_t* order, uint32_t p_lo, uint32_t p_hi, uint32_t q_lo, uint32_t q_hi,
-             uint32_t flags, uint64_t* counts, uint64_t* n_pairs, uint64_t* surv, uint64_t surv_cap,
-             uint64_t* n_surv, int threads) {
-  if (!T || !order || !counts || !n_pairs || !n_surv || p_lo == 0 || q_lo == 0 || p_lo > p_hi || q_lo > q_hi)
-    return -1;
+int pl_sieve_many(const pl_tables* T, const uint32_t* order, const pl_range* ranges, uint32_t n_ranges,
+                  uint64_t* counts, uint64_t* n_pairs, uint64_t* surv, uint32_t* surv_range, uint64_t surv_cap,
+                  uint64_t* n_surv, int threads) {
+  if (!T || !order || !ranges || !counts || !n_pairs || !n_surv) return -1;
   const uint32_t n = T->n;
   for (uint32_t i = 0; i < n; ++i)
     if (order[i] >= n) return -1;
+  uint64_t* row_end = (uint64_t*)malloc(sizeof(uint64_t) * (n_ranges ? n_ranges : 1));
+  if (!row_end) return -2;
+  uint64_t rows = 0;
+  for (uint32_t k = 0; k < n_ranges; ++k) {
+    const pl_range* R = &ranges[k];
+    if (R->p_lo == 0 || R->q_lo == 0 || R->p_lo > R->p_hi || R->q_lo > R->q_hi) {
+      free(row_end);
+      return -1;
+    }
+    rows += (uint64_t)R->p_hi - R->p_lo + 1;
+    row_end[k] = rows;
+  }
   int err = 0;
-  uint64_t pairs = 0, ns = 0, surv_pos = 0;
+  uint64_t ns = 0, surv_pos = 0;
 #ifdef _OPENMP
   if (threads > 0) omp_set_num_threads(threads);
 #else
   (void)threads;
 #endif
-#pragma omp parallel reduction(+ : pairs, ns)
+#pragma omp parallel reduction(+ : ns)
   {
-    uint64_t* my = (uint64_t*)calloc(n, sizeof(uint64_t));
-    uint32_t* pr = (uint32_t*)malloc(sizeof(uint32_t) * n);
-    const uint8_t** tab = (const uint8_t**)malloc(sizeof(void*) * n);
-    uint32_t* rr = (uint32_t*)malloc(sizeof(uint32_t) * n);
-    uint8_t* shared = NULL;
-    size_t shared_cap = 0;
-    const int ok = my && pr && tab && rr;
+    pl_scratch S = {0};
+    S.pr = (uint32_t*)malloc(sizeof(uint32_t) * n);
+    S.tab = (const uint8_t**)malloc(sizeof(void*) * n);
+    S.rr = (uint32_t*)malloc(sizeof(uint32_t) * n);
+    uint64_t* my = (uint64_t*)calloc((size_t)n_ranges * n, sizeof(uint64_t));
+    uint64_t* my_pairs = (uint64_t*)calloc(n_ranges ? n_ranges : 1, sizeof(uint64_t));
+    const int ok = S.pr && S.tab && S.rr && my && my_pairs;
     if (!ok) {
 #pragma omp atomic write
       err = -2;
     } else {
       for (uint32_t e = 0; e < n; ++e) {
-        tab[e] = T->bits[order[e]];
-        rr[e] = T->r[order[e]];
+        S.tab[e] = T->bits[order[e]];
+        S.rr[e] = T->r[order[e]];
       }
     }
     /* every thread reaches the work-sharing loop (a thread without memory skips its rows) */
 #pragma omp for schedule(dynamic, 1)
-    for (int64_t pp = (int64_t)p_hi; pp >= (int64_t)p_lo; --pp) {  /* long rows first */
+    for (int64_t it = 0; it < (int64_t)rows; ++it) {
       if (!ok) continue;
-      const uint32_t p = (uint32_t)pp;
-      uint32_t hi = q_hi;
-      if ((flags & 1u) && (uint64_t)hi >= p) hi = p - 1;
-      if (hi < q_lo) continue;
-      const size_t len = (size_t)hi - q_lo + 1;
-      if (len > shared_cap) {  /* q sharing a prime factor with p, marked per row */
-        free(shared);
-        shared = (uint8_t*)malloc(len);
-        shared_cap = shared ? len : 0;
-        if (!shared) {
+      uint32_t lo = 0, hi = n_ranges - 1;  /* the range holding work item it */
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (row_end[mid] > (uint64_t)it) hi = mid; else lo = mid + 1;
+      }
+      const pl_range* R = &ranges[lo];
+      const uint64_t first = lo ? row_end[lo - 1] : 0;
+      const uint32_t p = R->p_hi - (uint32_t)((uint64_t)it - first);  /* long rows first */
+      const int64_t k = sieve_row(R, p, n, &S, my + (size_t)lo * n, &ns, surv, surv_range, lo, surv_cap,
+                                  &surv_pos);
+      if (k < 0) {
 #pragma omp atomic write
-          err = -2;
-          continue;
-        }
-      }
-      memset(shared, 0, len);
-      uint32_t f[10];
-      const uint32_t nf = factors(p, f);
-      for (uint32_t j = 0; j < nf; ++j) {
-        const uint64_t first = ((uint64_t)q_lo + f[j] - 1) / f[j] * f[j];
-        for (uint64_t m = first; m <= hi; m += f[j]) shared[m - q_lo] = 1;
-      }
-      if (p >= q_lo && p <= hi) shared[p - q_lo] = 1;  /* p != q */
-      for (uint32_t e = 0; e < n; ++e) pr[e] = (p % rr[e]) * rr[e];
-      for (uint64_t q = q_lo; q <= hi; ++q) {
-        if (shared[q - q_lo]) continue;
-        ++pairs;
-        uint32_t e = 0;
-        for (; e < n; ++e) {  /* the first prime whose bit is set rejects the pair */
-          const uint32_t idx = pr[e] + (uint32_t)q % rr[e];
-          if ((tab[e][idx >> 3] >> (idx & 7)) & 1u) break;
-        }
-        if (e < n) {
-          ++my[e];
-        } else {
-          ++ns;
-          if (surv) {
-            uint64_t pos;
-#pragma omp atomic capture
-            pos = surv_pos++;
-            if (pos < surv_cap) surv[pos] = ((uint64_t)p << 32) | q;
-          }
-        }
+        err = -2;
+      } else {
+        my_pairs[lo] += (uint64_t)k;
       }
     }
     if (ok) {
 #pragma omp critical
-      for (uint32_t e = 0; e < n; ++e) counts[order[e]] += my[e];
+      {
+        for (uint32_t k = 0; k < n_ranges; ++k) {
+          n_pairs[k] += my_pairs[k];
+          for (uint32_t e = 0; e < n; ++e) counts[(size_t)k * n + order[e]] += my[(size_t)k * n + e];
+        }
+      }
     }
+    free(S.pr);
+    free(S.tab);
+    free(S.rr);
+    free(S.shared);
     free(my);
-    free(pr);
-    free(tab);
-    free(rr);
-    free(shared);
+    free(my_pairs);
   }
+  free(row_end);
   if (err) return err;
-  *n_pairs += pairs;
   *n_surv += ns;
   return 0;
+}
+
+/* One range (see pl_sieve_many): counts[n] and *n_pairs are ADDED to. */
+int pl_sieve(const pl_tables* T, const uint32_t* order, uint32_t p_lo, uint32_t p_hi, uint32_t q_lo, uint32_t q_hi,
+             uint32_t flags, uint64_t* counts, uint64_t* n_pairs, uint64_t* surv, uint64_t surv_cap,
+             uint64_t* n_surv, int threads) {
+  const pl_range R = {p_lo, p_hi, q_lo, q_hi, flags};
+  return pl_sieve_many(T, order, &R, 1, counts, n_pairs, surv, NULL, surv_cap, n_surv, threads);
 }
 
 /* Threads OpenMP uses by default (the host's cores unless limited). */

@@ -49,6 +49,10 @@ def _load():
         lib.pl_sieve.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), C.c_uint32, C.c_uint32, C.c_uint32,
                                  C.c_uint32, C.c_uint32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                                  C.POINTER(C.c_uint64), C.c_uint64, C.POINTER(C.c_uint64), C.c_int]
+        lib.pl_sieve_many.restype = C.c_int
+        lib.pl_sieve_many.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32,
+                                      C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                      C.POINTER(C.c_uint32), C.c_uint64, C.POINTER(C.c_uint64), C.c_int]
         lib.pl_max_threads.restype = C.c_int
         _lib = lib
     return _lib
@@ -106,3 +110,30 @@ class PaperLoop:
         k = min(n_surv.value, surv_cap)
         s = sorted((int(x) >> 32, int(x) & 0xFFFFFFFF) for x in surv[:k])
         return n_pairs.value, [int(c) for c in counts], s
+
+    def sieve_many(self, order, ranges, threads: int = 0, surv_cap: int = 1 << 20):
+        """[(n_pairs, counts in list order, sorted survivors)] of many ranges in one call;
+        the rows of all ranges are the OpenMP work items."""
+        n, k = len(self.primes), len(ranges)
+        flat = []
+        for rng in ranges:
+            if rng.get("allow_diagonal"):
+                raise ValueError("the paper loop sieves p != q only")
+            flat += [rng["p_lo"], rng["p_hi"], rng["q_lo"], rng["q_hi"], 1 if rng.get("q_lt_p") else 0]
+        arr = (C.c_uint32 * len(flat))(*flat)
+        order_a = (C.c_uint32 * n)(*order)
+        counts = (C.c_uint64 * (n * k))()
+        pairs = (C.c_uint64 * k)()
+        n_surv = C.c_uint64(0)
+        surv = (C.c_uint64 * max(1, surv_cap))()
+        surv_rng = (C.c_uint32 * max(1, surv_cap))()
+        st = _load().pl_sieve_many(self._h, order_a, arr, k, counts, pairs, surv, surv_rng, surv_cap,
+                                   C.byref(n_surv), int(threads))
+        if st:
+            raise RuntimeError(f"pl_sieve_many returned {st}")
+        m = min(n_surv.value, surv_cap)
+        per = [[] for _ in range(k)]
+        for i in range(m):
+            x = int(surv[i])
+            per[surv_rng[i]].append((x >> 32, x & 0xFFFFFFFF))
+        return [(int(pairs[j]), [int(c) for c in counts[j * n:(j + 1) * n]], sorted(per[j])) for j in range(k)]

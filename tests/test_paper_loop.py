@@ -85,3 +85,17 @@ def test_c2_in_full_equals_stored_oracle_result():
         n, counts, surv = L.sieve(gold["order"], gold["ranges"][0], threads=threads)
         r = gold["results"][0]
         assert n == r["n_pairs"] and counts == r["counts"] and surv == [tuple(x) for x in r["survivors"]]
+
+
+def test_many_ranges_in_one_call_equal_one_by_one():
+    """The multi-range call (rows of all ranges as work items) equals per-range calls and
+    the oracle on seeded rectangles of the batched workload's shape."""
+    primes = W.first_odd_primes(24)
+    L = PaperLoop(primes)
+    T = O.Tables(primes, "rate")
+    ranges = W.batched_rectangles(40, log2_area=(4.0, 12.0)) + [W.rect(1, 60, 1, 60)]
+    many = L.sieve_many(T.order, ranges)
+    for rng, got in zip(ranges, many):
+        assert got == L.sieve(T.order, rng)
+        want = O.sieve_range(T, rng)
+        assert got == (want[0], want[1], sorted(want[2]))
