@@ -273,9 +273,8 @@ int cuboid_result_free(cuboid_result* res);
 
 /* The batched sieve (all n ranges in one persistent launch, then the exact root test of
  * the survivors) for callers that may not allocate device memory when they sieve: a
- * loop with a latency budget (cudaMalloc and cudaFree synchronise the device), code
- * that records work into a CUDA graph, a host that only lends the library a fixed pool,
- * or a process at its memory limit.  This call allocates nothing and calls no
+ * loop with a latency budget (cudaMalloc and cudaFree synchronise the device), a host
+ * that only lends the library a fixed pool, or a process at its memory limit.  This call allocates nothing and calls no
  * allocating routine.  Its working memory (tile plans and the tile-queue/counter header,
  * 4096 x 32 bytes + 256 bytes) is one static array of device memory that every GPU that
  * loads the library holds until the process exits.  No paper counterpart: the paper

@@ -2,10 +2,9 @@
 //
 // Who needs it: code that must not call cudaMalloc / cudaFree at the moment it sieves.
 // A serving loop with a latency budget cannot afford them (both synchronise the device
-// and can stall for milliseconds); code that is recording CUDA work into a graph may not
-// allocate while it records; a host that embeds the library may hand it a fixed memory
-// pool and forbid any other device allocation; and a process at its memory limit has
-// nothing left to allocate.  For them the working memory the sieve needs besides its
+// and can stall for milliseconds); a host that embeds the library may hand it a fixed
+// memory pool and forbid any other device allocation; and a process at its memory limit
+// has nothing left to allocate.  For them the working memory the sieve needs besides its
 // inputs and outputs -- the tile plan of every range and the device header that holds
 // the tile-queue cursor and the survivor/root counters -- lives in one fixed array of
 // device memory that the library owns for as long as it is loaded.

@@ -1,7 +1,8 @@
 """The allocation-free sieve entry point against the regular one.
 
 cuboid_sieve_noalloc exists for callers that may not allocate device memory at the
-moment they sieve (latency-bound loops, graph recording, fixed pools, memory limits).
+moment they sieve (latency-bound loops, where cudaMalloc and cudaFree synchronise the
+device; hosts that lend the library a fixed pool; processes at their memory limit).
 All of its working memory is one static device array shared by every call, so this test
 runs it twice in a row on the same inputs and checks each call, output by output,
 against cuboid_sieve_batch: counts, pair totals, survivors and roots must be identical
@@ -99,5 +100,31 @@ def test_noalloc_rejects_too_many_ranges(env):
         n = cb.NOALLOC_MAX_RANGES + 1
         st = cb.cuboid_sieve_noalloc(t, 1, n, 1, 1, 0, 0, 0, 0, 0, 0, 1, stream)
         assert st == cb.ETOOLARGE
+    finally:
+        cb.cuboid_tables_free(t)
+
+
+def test_noalloc_at_full_capacity(env):
+    """Exactly CUBOID_NOALLOC_MAX_RANGES uneven one-row ranges: the plan fills the last
+    slot of the fixed array and the plan's prefix sum runs over more than 1024 ranges."""
+    import random
+    cb, torch, stream = env
+    primes = W.first_odd_primes(8)
+    g = random.Random(20160401)
+    ranges = []
+    for _ in range(cb.NOALLOC_MAX_RANGES):
+        p = g.randint(2, 1 << 20)
+        lo = g.randint(1, 1 << 20)
+        ranges.append(W.rect(p, p, lo, lo + g.choice([0, 1, 63, 64, 200, 1000, 5000])))
+    t = cb.cuboid_tables_build(primes, cb.ORDER_BY_RATE, stream)
+    try:
+        order = cb.cuboid_tables_order(t)
+        want = _expected(cb, t, len(primes), ranges, stream)
+        for _ in range(2):
+            got = _noalloc(cb, torch, t, len(primes), order, ranges, stream)
+            assert [g_["n_pairs"] for g_ in got] == [w["n_pairs"] for w in want]
+            assert [g_["counts"] for g_ in got] == [w["counts"] for w in want]
+            assert [g_["survivors"] for g_ in got] == [[tuple(x) for x in w["survivors"]] for w in want]
+            assert [g_["roots"] for g_ in got] == [[tuple(x) for x in w["roots"]] for w in want]
     finally:
         cb.cuboid_tables_free(t)
