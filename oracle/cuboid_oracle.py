@@ -168,9 +168,13 @@ class Tables:
     """Tables for a list of primes: full u_r for r <= FULL_TABLE_LIMIT, reduced v_r for
     every r, and the effective order (indices into the caller's list)."""
 
-    def __init__(self, primes, by_density: bool = False, full_limit: int = FULL_TABLE_LIMIT):
+    def __init__(self, primes, by_density: bool = False, full_limit: int = FULL_TABLE_LIMIT,
+                 reduced=None):
+        """``reduced``: the reduced tables ``reduced_table(r)`` of the primes, when they
+        were already computed (for instance by worker processes); else built here."""
         self.primes = [int(r) for r in primes]
-        self.reduced = [reduced_table(r) for r in self.primes]
+        self.reduced = ([np.asarray(v, dtype=np.uint8) for v in reduced] if reduced is not None
+                        else [reduced_table(r) for r in self.primes])
         self.full = [unsolvable_table(r) if r <= full_limit else None
                      for r in self.primes]
         self.inv = [np.array([0] + [pow(b, r - 2, r) for b in range(1, r)], dtype=np.int64)

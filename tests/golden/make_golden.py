@@ -1,7 +1,7 @@
 """Writes the stored expected values of the GPU parity tests.  Calls only the oracle and
 the seeded workload generators (no GPU code).  Run from the repository root:
 
-    python tests/golden/make_golden.py [sieve] [paper_files] [region]
+    python tests/golden/make_golden.py [sieve] [paper_files] [region] [c3_all] [c5_full] [c4_rate]
 
 Each output is JSON: {"config", "primes", "order", "ranges": [...], "results": [...]},
 one result per range: n_pairs, counts (caller order), survivors, roots.
@@ -54,7 +54,64 @@ def dump_region(name, p_from, p_to, primes):
     print(f"{name}: {time.time() - t0:.1f} s")
 
 
+def _sieve_chunk(args):
+    """Worker: oracle results of a list of (index, range) with the worker's tables."""
+    items = args
+    out = []
+    for k, rng in items:
+        n_pairs, counts, surv = O.sieve_range(_WORKER["T"], rng)
+        surv = sorted(surv)
+        roots = sorted((p, q, t) for (p, q) in surv for t in O.integer_roots(p, q))
+        out.append((k, {"n_pairs": n_pairs, "counts_nz": [[i, c] for i, c in enumerate(counts) if c],
+                        "survivors": surv, "roots": roots}))
+    return out
+
+
+_WORKER = {}
+
+
+def _init_worker(T):
+    _WORKER["T"] = T
+
+
+def dump_many(name, config, primes, ranges, mode, workers=None):
+    """Like dump, for thousands of ranges: rows sieved over every host core (spawned
+    processes, tables built once by the oracle and handed to each), counts stored sparse
+    as [[caller index, count], ...] (every other count is 0), gzip-compressed JSON."""
+    import gzip
+    import multiprocessing as mp
+    t0 = time.time()
+    ctx = mp.get_context("spawn")
+    workers = workers or os.cpu_count() or 1
+    with ctx.Pool(workers) as pool:
+        reduced = pool.map(O.reduced_table, primes)
+    T = O.Tables(primes, mode, full_limit=0, reduced=reduced)
+    # biggest first, dealt round robin in small chunks
+    idx = sorted(range(len(ranges)), key=lambda k: -W.lattice_points(ranges[k]))
+    chunks = [[(k, ranges[k]) for k in idx[j::workers * 8]] for j in range(workers * 8)]
+    results = [None] * len(ranges)
+    with ctx.Pool(workers, initializer=_init_worker, initargs=(T,)) as pool:
+        for part in pool.imap_unordered(_sieve_chunk, chunks):
+            for k, r in part:
+                results[k] = r
+    out = {"config": config, "primes": primes, "by_density": mode, "order": list(T.order),
+           "ranges": ranges, "results": results}
+    with gzip.open(os.path.join(HERE, name), "wt") as f:
+        json.dump(out, f, separators=(",", ":"))
+    print(f"{name}: {time.time() - t0:.1f} s")
+
+
 def main(which):
+    if "c3_all" in which:
+        c3 = W.c3()
+        dump_many("c3_all_rects.json.gz", "c3: all 4096 rectangles", c3["primes"], c3["ranges"], "rate")
+    if "c5_full" in which:
+        q = W.poisson_queries(1e3, 24, seed=W.DEFAULT_SEED + 77)
+        dump_many("c5_full_queries.json.gz", "c5: 24 queries of the full distribution (area 2^U(10,26), p, q < 2^24)",
+                  W.first_odd_primes(128), q, "rate")
+    if "c4_rate" in which:
+        dump("c4_rows_by_rate.json", "c4 sampled rows, rejection-rate order", W.first_odd_primes(256),
+             W.sampled_rows(1 << 20, 64), by_density="rate")
     if "region" in which:
         dump_region("region_112600_112699.json", 112600, 112699, W.primes_between(11, 541))
     if "paper_files" in which:
@@ -73,4 +130,4 @@ def main(which):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["sieve", "paper_files", "region"])
+    main(sys.argv[1:] or ["sieve", "paper_files", "region", "c3_all", "c5_full", "c4_rate"])

@@ -4,6 +4,7 @@ Survivor sets, roots, per-prime counts and pair totals must equal the oracle's o
 same seeded inputs.  Stored expected values under tests/golden/ were written by
 tests/golden/make_golden.py, which calls only the oracle.
 """
+import gzip
 import json
 import math
 import os
@@ -337,20 +338,67 @@ def test_c3_small_rectangles_vs_oracle(cb, stream):
         cb.cuboid_tables_free(t)
 
 
-def test_c3_batched_equals_plain(cb, stream):
-    """All 4096 rectangles of the batched workload: one persistent launch gives the same
-    per-range results as 4096 separate launches."""
+def _golden_gz(name):
+    """A gzip-compressed golden with sparse counts ([[caller index, count], ...])."""
+    with gzip.open(os.path.join(GOLDEN, name), "rt") as f:
+        g = json.load(f)
+    n = len(g["primes"])
+    for r in g["results"]:
+        c = [0] * n
+        for i, v in r.pop("counts_nz"):
+            c[i] = v
+        r["counts"] = c
+    return g
+
+
+def test_c3_all_rectangles_vs_oracle(cb, stream):
+    """All 4096 rectangles of the batched workload (1.05e9 pairs, 128 primes in
+    rejection-rate order), element by element against the oracle's stored results, in one
+    persistent launch and in 4096 separate launches."""
+    g = _golden_gz("c3_all_rects.json.gz")
     cfg = W.c3()
-    t = cb.cuboid_tables_build(cfg["primes"], 0, stream)
+    assert g["ranges"] == cfg["ranges"]
+    t = cb.cuboid_tables_build(g["primes"], cb.ORDER_BY_RATE, stream)
     try:
+        assert cb.cuboid_tables_order(t) == g["order"]
         st1, a = _run(cb, t, 128, cfg["ranges"], cb.MODE_BATCHED, stream)
         st2, b = _run(cb, t, 128, cfg["ranges"], cb.MODE_PLAIN, stream)
     finally:
         cb.cuboid_tables_free(t)
     assert st1 == st2 == cb.OK
-    assert a == b
-    for r, x in zip(cfg["ranges"], a):
-        assert sum(x["counts"]) + len(x["survivors"]) == x["n_pairs"]
+    _check_against(a, g["results"])
+    _check_against(b, g["results"])
+
+
+def test_c5_full_size_queries_vs_oracle(cb, stream):
+    """24 queries of the serving distribution at full size (areas up to 2^26, p, q < 2^24,
+    128 primes in rejection-rate order) against the oracle's stored results: batched
+    together, and one by one."""
+    g = _golden_gz("c5_full_queries.json.gz")
+    t = cb.cuboid_tables_build(g["primes"], cb.ORDER_BY_RATE, stream)
+    try:
+        st, a = _run(cb, t, 128, g["ranges"], cb.MODE_BATCHED, stream)
+        assert st == cb.OK
+        _check_against(a, g["results"])
+        for q, want in zip(g["ranges"], g["results"]):
+            st, one = _run(cb, t, 128, [q], cb.MODE_PLAIN, stream)
+            assert st == cb.OK
+            _check_against(one, [want])
+    finally:
+        cb.cuboid_tables_free(t)
+
+
+def test_c4_sampled_rows_rate_order(cb, stream):
+    """The 64 seeded C4 rows in the benchmark's order (rejection rate) against the oracle."""
+    g = _golden("c4_rows_by_rate.json")
+    t = cb.cuboid_tables_build(g["primes"], cb.ORDER_BY_RATE, stream)
+    try:
+        assert cb.cuboid_tables_order(t) == g["order"]
+        st, got = _run(cb, t, 256, g["ranges"], cb.MODE_BATCHED, stream)
+    finally:
+        cb.cuboid_tables_free(t)
+    assert st == cb.OK
+    _check_against(got, g["results"])
 
 
 def test_c4_sampled_rows(cb, stream):

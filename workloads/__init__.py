@@ -65,6 +65,11 @@ def triangle(n_max: int) -> dict:
     return rect(2, n_max, 1, n_max - 1, q_lt_p=True)
 
 
+def lattice_points(r: dict) -> int:
+    """Lattice points of a range's rectangle (its area; a size for scheduling work)."""
+    return (r["p_hi"] - r["p_lo"] + 1) * (r["q_hi"] - r["q_lo"] + 1)
+
+
 def c1() -> dict:
     return {"name": "c1_triangle200_24primes", "primes": first_odd_primes(24),
             "ranges": [triangle(200)]}
