@@ -53,6 +53,7 @@ extern "C" {
 #define CUBOID_EAGAIN     12  /* not finished yet (server poll) */
 #define CUBOID_EVERIFY    13  /* the exact root test could not settle a survivor */
 #define CUBOID_ETOOLARGE  14  /* more ranges than the fixed capacity of cuboid_sieve_noalloc */
+#define CUBOID_EINDEX     15  /* CUBOID_DEBUG build only: a kernel's index check failed (the access was skipped) */
 
 /* ------------------------------------------------------------ build flags */
 #define CUBOID_ORDER_AS_GIVEN    0x0u /* sieve the primes in the caller's order */
@@ -499,9 +500,24 @@ int cuboid_server_submit(cuboid_server* s, const cuboid_range* range, uint64_t* 
  * range (free it with cuboid_result_free); EINVAL for an unknown ticket. */
 int cuboid_server_poll(cuboid_server* s, uint64_t ticket, cuboid_result** out);
 
-/* Queue depth, queries admitted/refused/finished, batches launched (NULL-safe). */
+/* Queue depth, queries admitted/refused/finished, batches launched, and queries run again
+ * alone because their survivor or root records did not all fit in a shared batch
+ * (NULL-safe).  A query that still overflows alone finishes with EOVERFLOW (exact counts);
+ * the other queries of its first batch are not affected. */
 int cuboid_server_stats(const cuboid_server* s, uint64_t* in_flight, uint64_t* admitted,
-                        uint64_t* refused, uint64_t* finished, uint64_t* batches);
+                        uint64_t* refused, uint64_t* finished, uint64_t* batches, uint64_t* retried);
+
+/* Load replay (measurement of the request loop without a host language in the way):
+ * submits queries[i] at arrival_s[i] seconds after the call starts (non-decreasing; a
+ * refused submission is retried every 20 us and counted in *refused), then waits until all
+ * have finished.  Per query: tickets[i] (its result stays available to cuboid_server_poll),
+ * latency_s[i] from its admission to its result being on the host, npairs[i], status[i].
+ * *wall_s: from the call's start to the last result.  All of it within timeout_ms
+ * (ETIMEOUT otherwise; queries already admitted keep running).  Runs on the calling
+ * thread.  Errors: EINVAL, ERANGE (a bad query: the replay stops there), ETIMEOUT. */
+int cuboid_server_replay(cuboid_server* s, const cuboid_range* queries, const double* arrival_s, uint32_t n,
+                         uint32_t timeout_ms, uint64_t* tickets, double* latency_s, uint64_t* npairs,
+                         int32_t* status, double* wall_s, uint64_t* refused);
 
 /* Stop the loop (waits for work in flight, at most timeout_ms; ETIMEOUT otherwise). */
 int cuboid_server_destroy(cuboid_server* s, uint32_t timeout_ms);
@@ -509,11 +525,31 @@ int cuboid_server_destroy(cuboid_server* s, uint32_t timeout_ms);
 /* ================================================================ measurement */
 
 /* Integer-issue probe: launch `blocks` CTAs of `threads` threads, each thread running
- * `iters` iterations of 16 independent 32-bit integer ops (kind 0: IADD3/LOP3 mix,
- * kind 1: the sieve's lookup mix with shared-memory loads).  sink_dev: device buffer
- * of blocks*threads uint32 (defeats dead-code elimination).  Asynchronous. */
+ * `iters` iterations of 16 independent 32-bit integer ops (kind 0: add/shift/xor mix,
+ * kind 1: the sieve's lookup mix with shared-memory loads; kinds 2-7 one instruction per
+ * chain step: 2 lop3, 3 funnel shift, 4 popc followed by one mad.lo, 5 mad.lo, 6 mad.wide
+ * (32 x 32 + 64 bits), 7 mad.hi).  sink_dev: device buffer of blocks*threads uint32
+ * (defeats dead-code elimination).  Asynchronous. */
 int cuboid_probe_int_issue(uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
                            uint32_t* sink_dev, void* stream);
+
+/* Test probes of the arithmetic helpers (no paper counterpart; they check the library's
+ * own residue and modular routines against exact references).
+ *
+ * cuboid_probe_mod_min: for each modulus mods[i] (2 <= mods[i], n <= 65535) the sieve's
+ * residue routine (one mul.hi by floor(2^32 / r), one multiply-subtract and an unsigned
+ * minimum) is compared with the % operator on the GPU for every 32-bit n; mismatches[i]
+ * receives the number of n where they differ.  Host arrays; synchronous on stream.
+ *
+ * cuboid_probe_modarith: the root test's 62-bit arithmetic on the host (device = 0, the
+ * same routines compiled for the host) or on the GPU (device = 1), over host arrays:
+ * op 0: out[i] = a[i] b[i] mod m_j (Montgomery products); op 1: out[i] = a[i] mod m_j;
+ * op 2: out[i] = sign of the integer X, |X| < (m_0 ... m_{j-1} - 1) / 2, with residues
+ * a[i j + k] = X mod m_k (Garner), as 0, 1 or 2^64 - 1; op 3: out[k] = m_k, k < 14 (the
+ * moduli: the 14 largest primes below 2^62).  Errors: EINVAL, ECUDA. */
+int cuboid_probe_mod_min(const uint32_t* mods, uint32_t n, uint64_t* mismatches, void* stream);
+int cuboid_probe_modarith(uint32_t op, uint32_t j, const uint64_t* a, const uint64_t* b, uint32_t n,
+                          uint64_t* out, int device);
 
 /* Number of SMs of the current device and the library version string. */
 int cuboid_device_sms(uint32_t* sms);

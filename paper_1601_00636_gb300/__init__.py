@@ -16,7 +16,9 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libcuboid.so")
+# CUBOID_DEBUG=1 loads the debug build (index checks in the kernels; build.py --debug)
+DEBUG = os.environ.get("CUBOID_DEBUG", "") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "libcuboid_debug.so" if DEBUG else "libcuboid.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with paper_1601_00636_gb300/build.py "
@@ -25,10 +27,11 @@ _lib = C.CDLL(LIB_PATH)
 
 # ------------------------------------------------------------------ constants (cuboid.h)
 OK, EBUSY, ERANGE, EPMAX, EQLOW, EQHIGH, ENOTABLES, EINVAL, ENOMEM = 0, 1, 2, 3, 4, 5, 6, 7, 8
-ETIMEOUT, ECUDA, EOVERFLOW, EAGAIN, EVERIFY, ETOOLARGE = 9, 10, 11, 12, 13, 14
+ETIMEOUT, ECUDA, EOVERFLOW, EAGAIN, EVERIFY, ETOOLARGE, EINDEX = 9, 10, 11, 12, 13, 14, 15
 NOALLOC_MAX_RANGES = 4096
 STATUS_NAMES = {0: "OK", 1: "EBUSY", 2: "ERANGE", 3: "EPMAX", 4: "EQLOW", 5: "EQHIGH", 6: "ENOTABLES", 7: "EINVAL", 8: "ENOMEM",
-                9: "ETIMEOUT", 10: "ECUDA", 11: "EOVERFLOW", 12: "EAGAIN", 13: "EVERIFY", 14: "ETOOLARGE"}
+                9: "ETIMEOUT", 10: "ECUDA", 11: "EOVERFLOW", 12: "EAGAIN", 13: "EVERIFY", 14: "ETOOLARGE",
+                15: "EINDEX"}
 
 ORDER_AS_GIVEN, ORDER_BY_DENSITY, ORDER_BY_RATE = 0x0, 0x1, 0x4
 BUILD_REDUCED, BUILD_FULL = 0x0, 0x2
@@ -145,9 +148,15 @@ _SIGS = {
     "cuboid_server_submit": (C.c_int, [_P, C.POINTER(cuboid_range), C.POINTER(_u64)]),
     "cuboid_server_poll": (C.c_int, [_P, _u64, C.POINTER(_P)]),
     "cuboid_server_stats": (C.c_int, [_P, C.POINTER(_u64), C.POINTER(_u64), C.POINTER(_u64),
-                                      C.POINTER(_u64), C.POINTER(_u64)]),
+                                      C.POINTER(_u64), C.POINTER(_u64), C.POINTER(_u64)]),
+    "cuboid_server_replay": (C.c_int, [_P, C.c_void_p, C.POINTER(C.c_double), _u32, _u32, C.POINTER(_u64),
+                                       C.POINTER(C.c_double), C.POINTER(_u64), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_double), C.POINTER(_u64)]),
     "cuboid_server_destroy": (C.c_int, [_P, _u32]),
     "cuboid_probe_int_issue": (C.c_int, [_u32, _u32, _u32, _u32, _P, _P]),
+    "cuboid_probe_mod_min": (C.c_int, [C.POINTER(_u32), _u32, C.POINTER(_u64), _P]),
+    "cuboid_probe_modarith": (C.c_int, [_u32, _u32, C.POINTER(_u64), C.POINTER(_u64), _u32, C.POINTER(_u64),
+                                        C.c_int]),
     "cuboid_device_sms": (C.c_int, [C.POINTER(_u32)]),
     "cuboid_version": (C.c_char_p, []),
 }
@@ -598,9 +607,27 @@ def cuboid_server_poll(s, ticket: int):
 
 
 def cuboid_server_stats(s) -> dict:
-    v = [_u64() for _ in range(5)]
+    v = [_u64() for _ in range(6)]
     _check(_lib.cuboid_server_stats(s, *[C.byref(x) for x in v]), "cuboid_server_stats")
-    return dict(zip(("in_flight", "admitted", "refused", "finished", "batches"), [x.value for x in v]))
+    return dict(zip(("in_flight", "admitted", "refused", "finished", "batches", "retried"), [x.value for x in v]))
+
+
+def cuboid_server_replay(s, queries, arrival_s, timeout_ms: int = 600000) -> dict:
+    """Submit queries[i] at arrival_s[i] seconds (native loop), wait for all; returns
+    tickets, per-query latency (s), pairs and status, the wall time and refused retries.
+    The results stay available to cuboid_server_poll."""
+    n = len(queries)
+    arr = _ranges_array(queries) if n else (cuboid_range * 1)()
+    at = (C.c_double * max(n, 1))(*[float(x) for x in arrival_s])
+    tk = (_u64 * max(n, 1))()
+    lat = (C.c_double * max(n, 1))()
+    npairs = (_u64 * max(n, 1))()
+    st = (C.c_int32 * max(n, 1))()
+    wall, refused = C.c_double(), _u64()
+    _check(_lib.cuboid_server_replay(s, arr, at, n, timeout_ms, tk, lat, npairs, st, C.byref(wall),
+                                     C.byref(refused)), "cuboid_server_replay")
+    return {"tickets": list(tk[:n]), "latency_s": list(lat[:n]), "npairs": list(npairs[:n]),
+            "status": list(st[:n]), "wall_s": wall.value, "refused": refused.value}
 
 
 def cuboid_server_destroy(s, timeout_ms: int = 60000) -> int:
@@ -612,6 +639,26 @@ def cuboid_server_destroy(s, timeout_ms: int = 60000) -> int:
 def cuboid_probe_int_issue(kind, blocks, threads, iters, sink_dev_ptr: int, stream=None) -> None:
     _check(_lib.cuboid_probe_int_issue(kind, blocks, threads, iters, sink_dev_ptr, _stream(stream)),
            "cuboid_probe_int_issue")
+
+
+def cuboid_probe_mod_min(mods, stream=None) -> list[int]:
+    """Mismatches of the sieve's residue routine against % over every 32-bit n, per modulus."""
+    n = len(mods)
+    arr = (_u32 * n)(*[int(x) for x in mods])
+    out = (_u64 * n)()
+    _check(_lib.cuboid_probe_mod_min(arr, n, out, _stream(stream)), "cuboid_probe_mod_min")
+    return list(out)
+
+
+def cuboid_probe_modarith(op: int, j: int, a=(), b=(), device: bool = False) -> list[int]:
+    """The root test's modular arithmetic (see cuboid.h): op 0 a b mod m_j, op 1 a mod m_j,
+    op 2 Garner sign of residue vectors of length j (a flattened), op 3 the moduli."""
+    n = 14 if op == 3 else (len(a) // j if op == 2 else len(a))
+    aa = (_u64 * max(1, len(a)))(*[int(x) for x in a])
+    bb = (_u64 * max(1, len(b)))(*[int(x) for x in b])
+    out = (_u64 * max(1, n))()
+    _check(_lib.cuboid_probe_modarith(op, j, aa, bb, n, out, 1 if device else 0), "cuboid_probe_modarith")
+    return list(out[:n])
 
 
 def cuboid_device_sms() -> int:

@@ -14,6 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build", platform.machine())
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libcuboid.so")
+LIB_DEBUG = os.path.join(PKG, "libcuboid_debug.so")
 SOURCES = ["tables.cu", "plan.cu", "sieve.cu", "verify.cu", "runtime.cu", "server.cu", "noalloc.cu", "tune.cu", "region.cu", "tablefile.cu", "theorem.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -49,23 +50,29 @@ def _arch_of(path: str) -> str:
     return {62: "x86_64", 183: "aarch64"}.get(mach, str(mach))
 
 
-def build(verbose: bool = False, ptxas_verbose: bool = False, force: bool = False) -> str:
-    """Compile every source and link libcuboid.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, ptxas_verbose: bool = False, force: bool = False, debug: bool = False) -> str:
+    """Compile every source and link libcuboid.so (debug: libcuboid_debug.so, compiled with
+    CUBOID_DEBUG, whose kernels check their table, mask, factor and queue indices and
+    report a failed check as CUBOID_EINDEX); returns its path."""
+    build_dir = BUILD + ("-debug" if debug else "")
+    lib = LIB_DEBUG if debug else LIB
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         if force or ptxas_verbose or _stale(o, s):
             extra = ["-Xptxas", "-v"] if ptxas_verbose else []
+            if debug:
+                extra.append("-DCUBOID_DEBUG")
             jobs.append([cc, *_flags(extra), "-c", s, "-o", o])
 
     def run(cmd):
         p = subprocess.run(cmd, capture_output=True, text=True)
         return cmd, p
 
-    relink = bool(jobs) or not os.path.exists(LIB) or _arch_of(LIB) != platform.machine()
+    relink = bool(jobs) or not os.path.exists(lib) or _arch_of(lib) != platform.machine()
     with ThreadPoolExecutor(max_workers=min(8, max(1, len(jobs)))) as ex:
         for cmd, p in ex.map(run, jobs):
             if verbose or ptxas_verbose or p.returncode:
@@ -73,8 +80,8 @@ def build(verbose: bool = False, ptxas_verbose: bool = False, force: bool = Fals
             if p.returncode:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
     if relink:
-        objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
-        tmp = LIB + ".tmp"
+        objs = [os.path.join(build_dir, s.replace(".cu", ".o")) for s in SOURCES]
+        tmp = lib + ".tmp"
         cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
                "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
         p = subprocess.run(cmd, capture_output=True, text=True)
@@ -82,9 +89,10 @@ def build(verbose: bool = False, ptxas_verbose: bool = False, force: bool = Fals
             sys.stderr.write(" ".join(cmd) + "\n" + p.stdout + p.stderr)
         if p.returncode:
             raise RuntimeError("link failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, ptxas_verbose="--ptxas" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, ptxas_verbose="--ptxas" in sys.argv, force="-f" in sys.argv,
+                debug="--debug" in sys.argv))

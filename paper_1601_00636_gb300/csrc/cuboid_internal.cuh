@@ -74,12 +74,34 @@ struct DevHeader {
   unsigned int status;             // kStatus* bits
   unsigned int n_ranges;           // ranges of a batched launch
   unsigned long long stats[4];     // cuboid_stats fields
+  unsigned int debug_code;         // CUBOID_DEBUG builds: the first failed index check (0: none)
+  unsigned int debug_pad;
 };
 constexpr unsigned kStatusSurvOverflow = 1u;
 constexpr unsigned kStatusRootOverflow = 2u;
 constexpr unsigned kStatusBadRange = 4u;
 constexpr unsigned kStatusVerifyFail = 8u;
 constexpr unsigned kStatusStageTimeout = 16u;  // a CTA's shared-memory staging did not complete
+constexpr unsigned kStatusDebugIndex = 32u;    // CUBOID_DEBUG builds: an index check failed
+
+// Index checks of the CUBOID_DEBUG build: CUBOID_IDX_OK(cond, hdr, code) is true in a
+// release build; in a debug build it is cond, and when cond is false it records
+// kStatusDebugIndex and the first failing check's code in the header, and the caller skips
+// the access (no trap, no assert: the kernel finishes and the host reads the status).
+// Codes: 1 hot-prime window (shared), 2 cold window (shared), 3 cold window (global),
+// 4 coprimality mask entry, 5 factor record, 6 per-warp queue slot, 7 queue refill slot.
+#ifdef CUBOID_DEBUG
+__device__ __forceinline__ bool debug_index_ok(bool ok, DevHeader* hdr, unsigned code) {
+  if (!ok) {
+    atomicOr(&hdr->status, kStatusDebugIndex);
+    atomicCAS(&hdr->debug_code, 0u, code);
+  }
+  return ok;
+}
+#define CUBOID_IDX_OK(cond, hdr, code) ::cuboid::debug_index_ok((cond), (hdr), (code))
+#else
+#define CUBOID_IDX_OK(cond, hdr, code) true
+#endif
 
 // Odd trial-division primes below 2^16 with the exact-divisibility constants
 // inv = f^-1 mod 2^32 and lim = floor((2^32 - 1) / f):  f | n  <=>  n * inv <= lim.
@@ -197,6 +219,7 @@ struct SieveArgs {
   const cuboid_range* self_range = nullptr;
   cuboid_range self_range_val = {};
   uint32_t n_sms;               // SMs of the device (picks the register budget of the variant)
+  unsigned long long total_words = 0;  // window-row words of the tables (index checks of debug builds)
   // Piece of a 64-bit range: the planned y (word) coordinates are relative to y_base, a
   // multiple of 64 at or above 2^32 - 64, and every y of the piece is at least 2^32, above
   // any 32-bit row value x (so the piece holds no diagonal pair and no triangle edge).
@@ -222,7 +245,22 @@ struct VerifyArgs {
   uint32_t zero_words = 0;
   unsigned long long* zero_block2 = nullptr;
   uint32_t zero_words2 = 0;
+  // bits of the largest p or q any record can hold (picks the root test's moduli budget);
+  // 0: unknown (32-bit pairs, or pairs below 2^40 when base is set)
+  uint32_t max_bits = 0;
 };
+
+// Bits of the largest coordinate of n host ranges (0 for none).
+inline uint32_t ranges_max_bits(const cuboid_range* r, uint32_t n) {
+  uint32_t m = 0;
+  for (uint32_t i = 0; i < n; ++i) m |= r[i].p_hi | r[i].q_hi;
+  uint32_t b = 0;
+  while (m) {
+    ++b;
+    m >>= 1;
+  }
+  return b;
+}
 
 // Launchers (each checks its own launch and returns cudaError_t).
 cudaError_t launch_plan(const cuboid_range* ranges, uint32_t first, uint32_t count,

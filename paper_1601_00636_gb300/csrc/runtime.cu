@@ -147,6 +147,7 @@ LaunchShape launch_shape(const cuboid_tables* t, bool count_steps, bool wide) {
 void fill_hot(SieveArgs& a, const cuboid_tables* t, const LaunchShape& L) {
   a.n_hot = L.n_hot;
   a.n_sms = (uint32_t)t->sms;
+  a.total_words = t->total_words;
   a.row_lanes = L.row_lanes;
   a.stage_spins = kStageSpins;
   for (uint32_t h = 0; h < kMaxHot; ++h) {
@@ -289,7 +290,9 @@ static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, c
     if (timed) e = cudaEventRecord(r->tev[0], s);
     if (e == cudaSuccess) e = launch_sieve(sa, steps, L.blocks, L.threads, L.smem, s, false);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[1], s);
-    if (e == cudaSuccess) e = launch_verify(verify_args(r, true), verify_blocks(r->t), s, !timed);
+    VerifyArgs v = verify_args(r, true);
+    v.max_bits = h_ranges ? ranges_max_bits(h_ranges, 1) : 0u;
+    if (e == cudaSuccess) e = launch_verify(v, verify_blocks(r->t), s, !timed);
     if (timed) r->timed_launches = 1;
     return e;
   }
@@ -302,7 +305,9 @@ static cudaError_t run_kernels(cuboid_result* r, const cuboid_range* d_ranges, c
     if (e == cudaSuccess) e = launch_sieve(sa, steps, L.blocks, L.threads, L.smem, s, !timed);
     if (e == cudaSuccess && timed) e = cudaEventRecord(r->tev[2 * i + 1], s);
   }
-  if (e == cudaSuccess) e = launch_verify(verify_args(r, false), verify_blocks(r->t), s, !timed);
+  VerifyArgs v = verify_args(r, false);
+  v.max_bits = h_ranges ? ranges_max_bits(h_ranges, n) : 0u;
+  if (e == cudaSuccess) e = launch_verify(v, verify_blocks(r->t), s, !timed);
   if (timed) r->timed_launches = n;
   return e;
 }
@@ -620,7 +625,8 @@ int result_wait(cuboid_result* r) {
   r->stats.warp_steps = H.stats[2];
   r->stats.tiles = H.stats[3];
   int st = CUBOID_OK;
-  if (H.status & kStatusStageTimeout) st = CUBOID_ETIMEOUT;
+  if (H.status & kStatusDebugIndex) st = CUBOID_EINDEX;
+  else if (H.status & kStatusStageTimeout) st = CUBOID_ETIMEOUT;
   else if (H.status & kStatusVerifyFail) st = CUBOID_EVERIFY;
   else if (H.status & kStatusBadRange) st = CUBOID_ERANGE;
   else if (H.status & (kStatusSurvOverflow | kStatusRootOverflow)) st = CUBOID_EOVERFLOW;
@@ -908,6 +914,16 @@ static int verify_records(const std::vector<unsigned long long>& rec, const std:
     v.root_range = d_rr;
     v.root_cap = rcap;
     v.base = d_base;
+    unsigned long long m = 0;  // the largest coordinate of any record
+    for (uint32_t i = 0; i < n; ++i) {
+      const uint32_t k = rng ? (*rng)[i] : 0u;
+      const unsigned long long bp = base ? (*base)[2 * (size_t)k] : 0ull, bq = base ? (*base)[2 * (size_t)k + 1] : 0ull;
+      m |= ((rec[i] >> 32) + bp) | ((rec[i] & 0xFFFFFFFFull) + bq);
+    }
+    while (m) {
+      ++v.max_bits;
+      m >>= 1;
+    }
     e = launch_verify(v, (uint32_t)sms * 2, s);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&H, d_hdr, sizeof(H), cudaMemcpyDeviceToHost, s);
@@ -1076,8 +1092,43 @@ extern "C" int cuboid_shard_range(const cuboid_range* r, uint32_t k, uint32_t i,
 
 namespace {
 
+// One instruction of each kind per step of 16 independent chains (inline PTX, so the
+// compiler emits that instruction and nothing else in the chain): kinds 2-7.
+__device__ __forceinline__ uint32_t op_lop3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm volatile("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t op_shf(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm volatile("shf.r.wrap.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t op_popc_mad(uint32_t a, uint32_t k) {  // popc, then one mad
+  uint32_t d;
+  asm volatile("{\n .reg .b32 t;\n popc.b32 t, %1;\n mad.lo.u32 %0, t, %2, %1;\n}" : "=r"(d) : "r"(a), "r"(k));
+  return d;
+}
+__device__ __forceinline__ uint32_t op_mad(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long op_madwide(uint32_t a, uint32_t b, unsigned long long c) {
+  unsigned long long d;
+  asm volatile("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t op_madhi(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm volatile("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
 // kind 0: 16 independent chains of add / shift / xor (three 32-bit integer ops each).
 // kind 1: the sieve's lookup mix: shared-memory load pair, funnel shift, and, popc, xor.
+// kinds 2-7: one instruction per chain step: lop3, funnel shift, popc (+ one mad.lo),
+// mad.lo, mad.wide (32 x 32 + 64), mad.hi.
 __global__ void k_probe(uint32_t kind, uint32_t iters, uint32_t* sink) {
   __shared__ uint32_t tab[1024];
   for (uint32_t i = threadIdx.x; i < 1024; i += blockDim.x) tab[i] = i * 2654435761u;
@@ -1091,7 +1142,7 @@ __global__ void k_probe(uint32_t kind, uint32_t iters, uint32_t* sink) {
 #pragma unroll
       for (int i = 0; i < 16; ++i) a[i] = (a[i] + it) ^ (a[i] >> 1);
     }
-  } else {
+  } else if (kind == 1) {
     uint32_t acc = 0;
     for (uint32_t it = 0; it < iters; ++it) {
 #pragma unroll
@@ -1103,6 +1154,31 @@ __global__ void k_probe(uint32_t kind, uint32_t iters, uint32_t* sink) {
       }
     }
     a[0] += acc;
+  } else {
+    const uint32_t k1 = seed | 1u, k2 = seed ^ 0x9E3779B9u;
+    unsigned long long w[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) w[i] = a[i];
+#define CUBOID_PROBE_LOOP(stmt)            \
+  for (uint32_t it = 0; it < iters; ++it) { \
+    _Pragma("unroll") for (int i = 0; i < 16; ++i) { stmt; } \
+  }
+    if (kind == 2) {
+      CUBOID_PROBE_LOOP(a[i] = op_lop3(a[i], k1, it))
+    } else if (kind == 3) {
+      CUBOID_PROBE_LOOP(a[i] = op_shf(a[i], k2, it))
+    } else if (kind == 4) {
+      CUBOID_PROBE_LOOP(a[i] = op_popc_mad(a[i], k1))
+    } else if (kind == 5) {
+      CUBOID_PROBE_LOOP(a[i] = op_mad(a[i], k1, k2))
+    } else if (kind == 6) {
+      CUBOID_PROBE_LOOP(w[i] = op_madwide((uint32_t)w[i], k1, w[i]))
+    } else {
+      CUBOID_PROBE_LOOP(a[i] = op_madhi(a[i], k1, k2))
+    }
+#undef CUBOID_PROBE_LOOP
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] ^= (uint32_t)w[i] ^ (uint32_t)(w[i] >> 32);
   }
   uint32_t x = 0;
 #pragma unroll
@@ -1114,7 +1190,7 @@ __global__ void k_probe(uint32_t kind, uint32_t iters, uint32_t* sink) {
 
 extern "C" int cuboid_probe_int_issue(uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
                                       uint32_t* sink_dev, void* stream) {
-  if (kind > 1 || blocks == 0 || threads == 0 || threads > 1024 || threads % 32 || !sink_dev)
+  if (kind > 7 || blocks == 0 || threads == 0 || threads > 1024 || threads % 32 || !sink_dev)
     return CUBOID_EINVAL;
   k_probe<<<blocks, threads, 0, (cudaStream_t)stream>>>(kind, iters, sink_dev);
   return status_from_cuda(cudaGetLastError());

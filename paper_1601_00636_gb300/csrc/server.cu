@@ -6,7 +6,10 @@
 // persistent sieve launch (the batched path: device work queue, CUDA graph) on its own
 // stream, so batches admitted while others run overlap on the device.  Tables and the
 // per-stream result buffers stay resident; finished batches are split back into one
-// result per query, polled by ticket.  Every wait in the loop is bounded.
+// result per query, polled by ticket.  A query whose survivor or root records did not all
+// fit in its batch's buffers (its counts are exact, so the number of its survivors is
+// known) is run again alone instead of failing; the other queries of the batch keep their
+// results.  Every wait in the loop is bounded.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -26,6 +29,9 @@ int result_create(const cuboid_tables* t, uint32_t max_ranges, uint64_t surv_cap
 int sieve_into(cuboid_result* r, const cuboid_range* ranges, uint32_t n, uint32_t mode, cudaStream_t s,
                bool device_ranges, bool download);
 int result_wait(cuboid_result* r);
+int result_snapshot(cuboid_result* r, std::vector<unsigned long long>& counts,
+                    std::vector<unsigned long long>& npairs, unsigned long long& n_surv,
+                    unsigned long long& n_roots);
 cuboid_result* result_host_only(const cuboid_tables* t, uint64_t npairs, const uint64_t* counts,
                                 const uint64_t* surv, uint64_t n_surv, const cuboid_root* roots,
                                 uint64_t n_roots, int status);
@@ -41,9 +47,13 @@ constexpr uint64_t kSlotSurvCap = 1ull << 16;
 constexpr uint64_t kSlotRootCap = 1ull << 12;
 constexpr uint64_t kFreeMemMargin = 64ull << 20;
 
+using Clock = std::chrono::steady_clock;
+
 struct Query {
   uint64_t ticket;
   cuboid_range range;
+  Clock::time_point t_submit;
+  bool alone = false;  // run in a batch of its own (a retry after a record overflow)
 };
 
 struct Finished {
@@ -52,6 +62,7 @@ struct Finished {
   std::vector<uint64_t> surv;
   std::vector<cuboid_root> roots;
   int status = CUBOID_OK;
+  Clock::time_point t_submit, t_done;
 };
 
 struct Slot {
@@ -78,15 +89,18 @@ struct cuboid_server {
   std::thread worker;
   bool stop = false;
   uint64_t next_ticket = 1;
-  uint64_t in_flight = 0, admitted = 0, refused = 0, n_finished = 0, batches = 0;
+  uint64_t in_flight = 0, admitted = 0, refused = 0, n_finished = 0, batches = 0, retried = 0;
   uint64_t free_mem = ~0ull;
 };
 
 static void collect(cuboid_server* s, Slot& sl) {
   const int st = result_wait(sl.res);
   const uint32_t np = s->t->n;
-  std::vector<Finished> out(sl.queries.size());
-  for (size_t k = 0; k < sl.queries.size(); ++k) {
+  const size_t nq = sl.queries.size();
+  std::vector<Finished> out(nq);
+  std::vector<char> again(nq, 0);
+  uint64_t roots_kept = 0;
+  for (size_t k = 0; k < nq; ++k) {
     Finished& f = out[k];
     f.counts.resize(np);
     uint64_t ns = 0, nr = 0;
@@ -96,11 +110,45 @@ static void collect(cuboid_server* s, Slot& sl) {
     f.surv.assign(sv, sv + ns);
     f.roots.assign(rv, rv + nr);
     f.status = st;
+    f.t_submit = sl.queries[k].t_submit;
+    roots_kept += nr;
   }
+  if (st == CUBOID_EOVERFLOW) {
+    // Counts are exact, so a query's survivors number its pairs minus its counts: a query
+    // that got all of them (and, if root records were dropped, has no survivor) is
+    // complete; any other runs again alone (or, alone already, keeps EOVERFLOW).
+    std::vector<unsigned long long> c, npr;
+    unsigned long long ns_all = 0, nr_all = 0;
+    result_snapshot(sl.res, c, npr, ns_all, nr_all);
+    const bool roots_dropped = nr_all > roots_kept;
+    for (size_t k = 0; k < nq; ++k) {
+      Finished& f = out[k];
+      uint64_t rejected = 0;
+      for (uint64_t x : f.counts) rejected += x;
+      const uint64_t want = f.npairs - rejected;
+      const bool complete = f.surv.size() == want && !(roots_dropped && want > 0);
+      if (complete) f.status = CUBOID_OK;
+      else if (nq > 1) again[k] = 1;
+    }
+  }
+  const auto now = Clock::now();
   std::lock_guard<std::mutex> lk(s->mu);
-  for (size_t k = 0; k < sl.queries.size(); ++k) s->finished[sl.queries[k].ticket] = std::move(out[k]);
-  s->in_flight -= sl.queries.size();
-  s->n_finished += sl.queries.size();
+  size_t n_again = 0;
+  for (size_t k = nq; k-- > 0;) {  // retries go to the front, in their order
+    if (!again[k]) continue;
+    Query q = sl.queries[k];
+    q.alone = true;
+    s->pending.push_front(q);
+    ++n_again;
+  }
+  for (size_t k = 0; k < nq; ++k) {
+    if (again[k]) continue;
+    out[k].t_done = now;
+    s->finished[sl.queries[k].ticket] = std::move(out[k]);
+  }
+  s->retried += n_again;
+  s->in_flight -= nq - n_again;
+  s->n_finished += nq - n_again;
   sl.queries.clear();
   sl.busy = false;
 }
@@ -132,8 +180,11 @@ static void dispatcher(cuboid_server* s) {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->pending.empty()) break;
         while (!s->pending.empty() && sl.queries.size() < s->batch_cap) {
+          // a retried query runs in a batch of its own
+          if (s->pending.front().alone && !sl.queries.empty()) break;
           sl.queries.push_back(s->pending.front());
           s->pending.pop_front();
+          if (sl.queries.back().alone) break;
         }
       }
       batch.clear();
@@ -148,6 +199,8 @@ static void dispatcher(cuboid_server* s) {
           Finished f;
           f.counts.assign(s->t->n, 0);
           f.status = st;
+          f.t_submit = q.t_submit;
+          f.t_done = Clock::now();
           s->finished[q.ticket] = std::move(f);
         }
         s->in_flight -= sl.queries.size();
@@ -234,7 +287,7 @@ extern "C" int cuboid_server_submit(cuboid_server* s, const cuboid_range* range,
     return CUBOID_EBUSY;
   }
   const uint64_t tk = s->next_ticket++;
-  s->pending.push_back(Query{tk, R});
+  s->pending.push_back(Query{tk, R, Clock::now(), false});
   s->in_flight++;
   s->admitted++;
   *ticket = tk;
@@ -267,7 +320,8 @@ extern "C" int cuboid_server_poll(cuboid_server* s, uint64_t ticket, cuboid_resu
 }
 
 extern "C" int cuboid_server_stats(const cuboid_server* s, uint64_t* in_flight, uint64_t* admitted,
-                                   uint64_t* refused, uint64_t* finished, uint64_t* batches) {
+                                   uint64_t* refused, uint64_t* finished, uint64_t* batches,
+                                   uint64_t* retried) {
   if (!s) return CUBOID_EINVAL;
   cuboid_server* m = const_cast<cuboid_server*>(s);
   std::lock_guard<std::mutex> lk(m->mu);
@@ -276,7 +330,67 @@ extern "C" int cuboid_server_stats(const cuboid_server* s, uint64_t* in_flight, 
   if (refused) *refused = s->refused;
   if (finished) *finished = s->n_finished;
   if (batches) *batches = s->batches;
+  if (retried) *retried = s->retried;
   return CUBOID_OK;
+}
+
+extern "C" int cuboid_server_replay(cuboid_server* s, const cuboid_range* queries, const double* arrival_s,
+                                    uint32_t n, uint32_t timeout_ms, uint64_t* tickets, double* latency_s,
+                                    uint64_t* npairs, int32_t* status, double* wall_s, uint64_t* refused) {
+  if (!s || (n && (!queries || !arrival_s || !tickets || !latency_s || !npairs || !status)) || !wall_s ||
+      !refused)
+    return CUBOID_EINVAL;
+  for (uint32_t i = 1; i < n; ++i)
+    if (!(arrival_s[i] >= arrival_s[i - 1])) return CUBOID_EINVAL;
+  const auto t0 = Clock::now();
+  const auto limit = t0 + std::chrono::milliseconds(timeout_ms);
+  auto since = [&](Clock::time_point t) { return std::chrono::duration<double>(t - t0).count(); };
+  uint64_t busy = 0;
+  uint32_t i = 0;
+  while (i < n) {
+    const double now = since(Clock::now());
+    bool refused_now = false;
+    while (i < n && arrival_s[i] <= now) {
+      const int st = cuboid_server_submit(s, &queries[i], &tickets[i]);
+      if (st == CUBOID_EBUSY) {  // admission refused: the query waits, the clock runs on
+        ++busy;
+        refused_now = true;
+        break;
+      }
+      if (st != CUBOID_OK) return st;
+      ++i;
+    }
+    if (Clock::now() > limit) return CUBOID_ETIMEOUT;
+    if (i >= n) break;
+    const double gap = refused_now ? 20e-6 : arrival_s[i] - since(Clock::now());
+    if (gap > 200e-6)
+      std::this_thread::sleep_for(std::chrono::duration<double>(gap - 100e-6));
+    else if (gap > 0)
+      std::this_thread::yield();
+  }
+  // every query finished (its result stays for cuboid_server_poll)
+  for (;;) {
+    uint32_t done = 0;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (uint32_t k = 0; k < n; ++k) done += s->finished.count(tickets[k]) ? 1u : 0u;
+      if (done == n) {
+        double last = 0.0;
+        for (uint32_t k = 0; k < n; ++k) {
+          const Finished& f = s->finished[tickets[k]];
+          latency_s[k] = std::chrono::duration<double>(f.t_done - f.t_submit).count();
+          npairs[k] = f.npairs;
+          status[k] = f.status;
+          last = std::max(last, since(f.t_done));
+        }
+        *wall_s = last;
+        *refused = busy;
+        return CUBOID_OK;
+      }
+    }
+    if (Clock::now() > limit) return CUBOID_ETIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
 }
 
 extern "C" int cuboid_server_destroy(cuboid_server* s, uint32_t timeout_ms) {

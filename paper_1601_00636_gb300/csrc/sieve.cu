@@ -117,12 +117,16 @@ __device__ __forceinline__ void cold_batch(const SieveArgs& a, const PrimeInfo* 
       s = min(s, s - pi.r);
     }
     const uint32_t wi = ro + (s >> 5);
-    uint32_t w0, w1, w2;
+    uint32_t w0 = 0, w1 = 0, w2 = 0;
+    // the window stays inside row (x mod r): s < r and its last word before the row's end
+    const bool in_row = s < pi.r && (s >> 5) + 2 < pi.W;
     if (i < a.n_smem_primes) {
-      w0 = s_tab[wi];
-      w1 = s_tab[wi + 1];
-      w2 = s_tab[wi + 2];
-    } else {
+      if (CUBOID_IDX_OK(in_row && wi + 2 < a.smem_words, a.hdr, 2u)) {
+        w0 = s_tab[wi];
+        w1 = s_tab[wi + 1];
+        w2 = s_tab[wi + 2];
+      }
+    } else if (CUBOID_IDX_OK(in_row && wi + 2 < a.total_words, a.hdr, 3u)) {
       w0 = __ldg(a.words + wi);
       w1 = __ldg(a.words + wi + 1);
       w2 = __ldg(a.words + wi + 2);
@@ -182,9 +186,10 @@ __device__ __forceinline__ void drain(const SieveArgs& a, const PrimeInfo* s_inf
                               st_warpsteps);
     const uint32_t rest = qn - cnt;
     uint4 e = make_uint4(0u, 0u, 0u, 0u);
-    if (lane < rest) e = q[32 + lane];
+    const bool mv = lane < rest && CUBOID_IDX_OK(32 + lane < kQueue, a.hdr, 7u);
+    if (mv) e = q[32 + lane];
     __syncwarp();
-    if (lane < rest) q[lane] = e;
+    if (mv) q[lane] = e;
     __syncwarp();
     qn = rest;
   }
@@ -467,10 +472,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           }
           const uint32_t pos = nfo + __popc(bal & lanemask_lt);
           const uint32_t f = tp.f;
-          s_fac[pos] = make_uint4(f, mod_min(kStride, f, tp.lim), f < kPeriodicBelow ? s_foff[f] : kBitTab,
-                                  f < kPeriodicBelow ? f - 1 : 128u);
-          s_fmag[pos] = tp.lim;  // floor(2^32 / f) for odd f > 1
-          if constexpr (kWide) s_fyb[pos] = (uint32_t)(a.y_base % f);
+          if (CUBOID_IDX_OK(pos < kMaxFactors, a.hdr, 5u)) {
+            s_fac[pos] = make_uint4(f, mod_min(kStride, f, tp.lim), f < kPeriodicBelow ? s_foff[f] : kBitTab,
+                                    f < kPeriodicBelow ? f - 1 : 128u);
+            s_fmag[pos] = tp.lim;  // floor(2^32 / f) for odd f > 1
+            if constexpr (kWide) s_fyb[pos] = (uint32_t)(a.y_base % f);
+          }
         }
 #pragma unroll
         for (int d = G / 2; d; d >>= 1) pw *= __shfl_xor_sync(FULL, pw, d);  // within the group
@@ -481,7 +488,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         nfo += __popc(bal);
       }
       if (live && m > 1) {  // a prime: above every trial prime tested, or below 9 if no batch ran
-        if (gl == 0) {
+        if (gl == 0 && CUBOID_IDX_OK(nfo < kMaxFactors, a.hdr, 5u)) {
           const uint32_t mag = 0xFFFFFFFFu / m;
           s_fac[nfo] = make_uint4(m, mod_min(kStride, m, mag), m < kPeriodicBelow ? s_foff[m] : kBitTab,
                                   m < kPeriodicBelow ? m - 1 : 128u);
@@ -559,7 +566,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     auto enqueue = [&](uint32_t al, uint32_t ah, uint32_t y0) {
       const uint32_t bal = __ballot_sync(FULL, (al | ah) != 0u);
       if (bal) {
-        if (al | ah) s_queue[qn + __popc(bal & lanemask_lt)] = make_uint4(x, y0, al, ah);
+        const uint32_t slot = qn + __popc(bal & lanemask_lt);
+        if ((al | ah) && CUBOID_IDX_OK(slot < kQueue, a.hdr, 6u)) s_queue[slot] = make_uint4(x, y0, al, ah);
         qn += __popc(bal);
         __syncwarp();
         drain<kSteps, kWide>(a, s_info, s_tab, s_ybr, wcnt, s_queue, qn, K, rows_q, k, lane, ws, st_wsteps,
@@ -576,7 +584,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
 #pragma unroll
         for (int i = 0; i < kFacRegs; ++i) {  // inert entries give an empty mask
           const uint4 fc = s_fac[i];          // {f, (128 G) mod f, table base, cap}
-          const uint4 mk = s_mtab[fc.z + min(tf[i], fc.w)];
+          const uint32_t mi = fc.z + min(tf[i], fc.w);
+          const uint4 mk = CUBOID_IDX_OK(mi < kMaskTab, a.hdr, 4u) ? s_mtab[mi] : make_uint4(0u, 0u, 0u, 0u);
           m.x |= mk.x;
           m.y |= mk.y;
           m.z |= mk.z;
@@ -592,7 +601,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
             s = (uint32_t)(ss >= fc.x ? ss - fc.x : ss);
           }
           const uint32_t t = s ? fc.x - s : 0u;
-          const uint4 mk = s_mtab[fc.z + min(t, fc.w)];
+          const uint32_t mi = fc.z + min(t, fc.w);
+          const uint4 mk = CUBOID_IDX_OK(mi < kMaskTab, a.hdr, 4u) ? s_mtab[mi] : make_uint4(0u, 0u, 0u, 0u);
           m.x |= mk.x;
           m.y |= mk.y;
           m.z |= mk.z;
@@ -610,7 +620,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         const uint32_t sn = s + a.hot_step[h];  // next pair: + (128 G) mod r, below 2r
         sh[h] = min(sn, sn - a.hot_r[h]);
         const uint32_t* tp = s_tab + rb[h] + (s >> 5);
-        const uint32_t w0 = tp[0], w1 = tp[1], w2 = tp[2], w3 = tp[3], w4 = tp[4];
+        uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0;
+        // the window stays inside row (x mod r): s < r, its last word before the row's end
+        if (CUBOID_IDX_OK(s < a.hot_r[h] && (s >> 5) + 4 < a.hot_W[h] && rb[h] + (s >> 5) + 4 < a.smem_words,
+                          a.hdr, 1u)) {
+          w0 = tp[0];
+          w1 = tp[1];
+          w2 = tp[2];
+          w3 = tp[3];
+          w4 = tp[4];
+        }
         alA &= ~__funnelshift_r(w0, w1, s);  // the window of u_r(x mod r, y0 mod r ...)
         ahA &= ~__funnelshift_r(w1, w2, s);
         alB &= ~__funnelshift_r(w2, w3, s);
@@ -702,6 +721,22 @@ cudaError_t launch_k(const SieveArgs& a, uint32_t blocks, uint32_t threads, uint
   return launch_m<S, 1024>(a, blocks, threads, smem, s, pdl);
 }
 
+// Exhaustive check of mod_min: every 32-bit n against the % operator for modulus
+// mods[blockIdx.y] (2 <= r < 2^32) with the reciprocal floor(2^32 / r) the tables use
+// (floor((2^32 - 1) / r) for the factors, the same value for every r that is not a
+// power of two).  bad[y] counts the mismatches.
+__global__ void k_probe_mod_min(const uint32_t* mods, unsigned long long* bad) {
+  const uint32_t r = mods[blockIdx.y];
+  const uint32_t magic = (uint32_t)((1ull << 32) / r);
+  unsigned long long miss = 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long n = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; n < (1ull << 32);
+       n += stride)
+    miss += mod_min((uint32_t)n, r, magic) != (uint32_t)n % r;
+  miss = warp_sum_u64(miss);
+  if ((threadIdx.x & 31) == 0 && miss) atomicAdd(bad + blockIdx.y, miss);
+}
+
 }  // namespace
 
 size_t sieve_smem_bytes(uint32_t smem_words, uint32_t n_primes, uint32_t threads, uint32_t row_lanes, bool wide) {
@@ -743,3 +778,30 @@ cudaError_t launch_sieve(const SieveArgs& a, bool count_steps, uint32_t blocks, 
 }
 
 }  // namespace cuboid
+
+extern "C" int cuboid_probe_mod_min(const uint32_t* mods, uint32_t n, uint64_t* mismatches, void* stream) {
+  using namespace cuboid;
+  if (!mods || !mismatches || n == 0 || n > 65535) return CUBOID_EINVAL;
+  for (uint32_t i = 0; i < n; ++i)
+    if (mods[i] < 2) return CUBOID_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* d_mods = nullptr;
+  unsigned long long* d_bad = nullptr;
+  cudaError_t e = cudaMalloc(&d_mods, n * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&d_bad, n * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_mods, mods, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, n * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_probe_mod_min<<<dim3((unsigned)sms * 8, n), 256, 0, s>>>(d_mods, d_bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(mismatches, d_bad, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_mods);
+  cudaFree(d_bad);
+  return status_from_cuda(e);
+}

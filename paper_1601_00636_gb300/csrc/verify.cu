@@ -32,6 +32,7 @@ namespace {
 
 typedef unsigned long long ull;
 constexpr int kMaxMod = 14;  // 61 * 14 >= 37 + 20 * 40: M below 2^40
+static_assert((37 + 20 * 40 + 60) / 61 == kMaxMod, "moduli for 40-bit pairs");
 constexpr int kMaxCells = 24;
 // Threads per CTA of the root test (two CTAs per SM).  The large helpers (context set-up,
 // exact sign, FP64 proposal, bracket stretch) are kept out of line: inlined, the kernel's
@@ -48,27 +49,59 @@ __constant__ ull c_ginv[kMaxMod][kMaxMod];  // Montgomery form of m_i^-1 mod m_j
 
 // ---------------------------------------------------------------- Montgomery arithmetic
 
-__device__ __forceinline__ ull mmul(ull a, ull b, const ModConst& M) {
-  const ull lo = a * b, hi = __umul64hi(a, b);
+// High 64 bits of a 64 x 64-bit product (the host build serves the host-side tests).
+__host__ __device__ __forceinline__ ull mulhi64(ull a, ull b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (ull)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// Montgomery product a b 2^-64 mod m for a, b < m < 2^62.
+__host__ __device__ __forceinline__ ull mmul(ull a, ull b, const ModConst& M) {
+  const ull lo = a * b, hi = mulhi64(a, b);
   const ull u = lo * M.minv;
-  const ull uhi = __umul64hi(u, M.m);
+  const ull uhi = mulhi64(u, M.m);
   const ull t = hi + uhi + (lo != 0ull);
   return t >= M.m ? t - M.m : t;
 }
-__device__ __forceinline__ ull madd(ull a, ull b, ull m) {
+__host__ __device__ __forceinline__ ull madd(ull a, ull b, ull m) {
   const ull s = a + b;
   return s >= m ? s - m : s;
 }
-__device__ __forceinline__ ull msub(ull a, ull b, ull m) { return a >= b ? a - b : a + (m - b); }
+__host__ __device__ __forceinline__ ull msub(ull a, ull b, ull m) { return a >= b ? a - b : a + (m - b); }
 // v mod m for any 64-bit v when 2^61 < m < 2^62 (v < 8 m).
-__device__ __forceinline__ ull red64(ull v, ull m) {
+__host__ __device__ __forceinline__ ull red64(ull v, ull m) {
   if (v >= 4 * m) v -= 4 * m;
   if (v >= 2 * m) v -= 2 * m;
   if (v >= m) v -= m;
   return v;
 }
-__device__ __forceinline__ ull tomont(ull x, const ModConst& M) { return mmul(red64(x, M.m), M.r2, M); }
-__device__ __forceinline__ ull frommont(ull x, const ModConst& M) { return mmul(x, 1ull, M); }
+__host__ __device__ __forceinline__ ull tomont(ull x, const ModConst& M) { return mmul(red64(x, M.m), M.r2, M); }
+__host__ __device__ __forceinline__ ull frommont(ull x, const ModConst& M) { return mmul(x, 1ull, M); }
+
+// Sign of the integer X with |X| < (prod m_j - 1) / 2 whose residues modulo m_0..m_{K-1}
+// are x[j] (Montgomery form; not all zero): Garner's mixed-radix digits v_j, compared
+// with those of (prod m_j - 1) / 2 from the most significant digit down.  ginv[i][j] is
+// m_i^-1 mod m_j in Montgomery form.
+template <int KM>
+__host__ __device__ __forceinline__ int garner_sign(const ull* x, int K, const ModConst* mods,
+                                                    const ull (*ginv)[kMaxMod]) {
+  ull v[KM];
+  v[0] = frommont(x[0], mods[0]);
+  for (int j = 1; j < K; ++j) {
+    const ModConst M = mods[j];
+    ull t = x[j];
+    for (int i = 0; i < j; ++i) t = mmul(msub(t, tomont(v[i], M), M.m), ginv[i][j], M);
+    v[j] = frommont(t, M);
+  }
+  for (int j = K - 1; j >= 0; --j) {
+    const ull h = mods[j].half;
+    if (v[j] != h) return v[j] > h ? -1 : 1;
+  }
+  return 1;
+}
 
 // ---------------------------------------------------------------- 192-bit unsigned
 
@@ -143,10 +176,20 @@ __device__ __forceinline__ ull umod_mont(const U192& u, const ModConst& M) {
 
 // ---------------------------------------------------------------- per-pair context
 
+// Coefficient k of R^(d) (d <= k <= 5) sits at cidx(d, k): 20 entries per modulus.
+__host__ __device__ constexpr int cidx(int d, int k) { return (d == 0 ? 0 : d == 1 ? 6 : d == 2 ? 11 : d == 3 ? 15 : 18) + k - d; }
+constexpr int kCoef = 20;
+
+// Moduli a survivor with max(p, q) of `bits` bits needs: 61 K >= 37 + 20 bits.
+__host__ __device__ constexpr int moduli_for_bits(int bits) { return (37 + 20 * bits + 60) / 61; }
+
+// Per-pair context for at most KM moduli (the root-test kernel is instantiated per KM, so
+// its per-thread local memory is sized for the survivors of the launch, not for 2^40).
+template <int KM>
 struct Ctx {
   int K;
-  ull co[kMaxMod][5][6];  // Montgomery coefficient of u^(k-d) in R^(d), index [j][d][k]
-  double dco[5][6];       // FP64 version
+  ull co[KM][kCoef];  // Montgomery coefficient of u^(k-d) in R^(d), modulus j: co[j][cidx(d, k)]
+  double dco[kCoef];  // FP64 version
 };
 
 // a_0..a_5 of R (Eq. 1.1 with u = t^2) modulo m, Montgomery form.
@@ -199,11 +242,13 @@ __device__ __forceinline__ double falling(int k, int d) {
   return f;
 }
 
-__device__ __noinline__ void ctx_init(Ctx& C, ull p, ull q) {
+// Returns false (and sets nothing) when the pair needs more than KM moduli.
+template <int KM>
+__device__ __noinline__ bool ctx_init(Ctx<KM>& C, ull p, ull q) {
   const ull M = p > q ? p : q;
   const int bits = 64 - __clzll((long long)M);
-  int K = (37 + 20 * bits + 60) / 61;
-  if (K > kMaxMod) K = kMaxMod;
+  const int K = moduli_for_bits(bits);
+  if (K > KM) return false;
   C.K = K;
   for (int j = 0; j < K; ++j) {
     const ModConst Mc = c_mod[j];
@@ -211,51 +256,42 @@ __device__ __noinline__ void ctx_init(Ctx& C, ull p, ull q) {
     r_coeffs_mod(p, q, Mc, a);
     for (int d = 0; d < 5; ++d)
       for (int kk = d; kk <= 5; ++kk)
-        C.co[j][d][kk] = mmul(a[kk], tomont((ull)falling(kk, d), Mc), Mc);
+        C.co[j][cidx(d, kk)] = mmul(a[kk], tomont((ull)falling(kk, d), Mc), Mc);
   }
   double a[6];
   r_coeffs_f64((double)p, (double)q, a);
   for (int d = 0; d < 5; ++d)
-    for (int kk = d; kk <= 5; ++kk) C.dco[d][kk] = a[kk] * falling(kk, d);
+    for (int kk = d; kk <= 5; ++kk) C.dco[cidx(d, kk)] = a[kk] * falling(kk, d);
+  return true;
 }
 
 // Exact sign of R^(d)(u), 0 <= u <= U.
-__device__ __noinline__ int exact_sign(const Ctx& C, int d, const U192& u) {
-  ull x[kMaxMod], v[kMaxMod];
+template <int KM>
+__device__ __noinline__ int exact_sign(const Ctx<KM>& C, int d, const U192& u) {
+  ull x[KM];
   bool allzero = true;
   for (int j = 0; j < C.K; ++j) {
     const ModConst M = c_mod[j];
     const ull um = umod_mont(u, M);
-    ull acc = C.co[j][d][5];
-    for (int kk = 4; kk >= d; --kk) acc = madd(mmul(acc, um, M), C.co[j][d][kk], M.m);
+    ull acc = C.co[j][cidx(d, 5)];
+    for (int kk = 4; kk >= d; --kk) acc = madd(mmul(acc, um, M), C.co[j][cidx(d, kk)], M.m);
     x[j] = acc;
     allzero &= (acc == 0);
   }
   if (allzero) return 0;
-  // Garner: mixed-radix digits v_j of the residue vector
-  v[0] = frommont(x[0], c_mod[0]);
-  for (int j = 1; j < C.K; ++j) {
-    const ModConst M = c_mod[j];
-    ull t = x[j];
-    for (int i = 0; i < j; ++i) t = mmul(msub(t, tomont(v[i], M), M.m), c_ginv[i][j], M);
-    v[j] = frommont(t, M);
-  }
-  // value > (prod m - 1)/2  <=>  digits above those of (m_j - 1)/2, most significant first
-  for (int j = C.K - 1; j >= 0; --j) {
-    const ull h = c_mod[j].half;
-    if (v[j] != h) return v[j] > h ? -1 : 1;
-  }
-  return 1;
+  return garner_sign<KM>(x, C.K, c_mod, c_ginv);
 }
 
-__device__ double fval(const Ctx& C, int d, double u) {
-  double acc = C.dco[d][5];
-  for (int kk = 4; kk >= d; --kk) acc = acc * u + C.dco[d][kk];
+template <int KM>
+__device__ double fval(const Ctx<KM>& C, int d, double u) {
+  double acc = C.dco[cidx(d, 5)];
+  for (int kk = 4; kk >= d; --kk) acc = acc * u + C.dco[cidx(d, kk)];
   return acc;
 }
 
+template <int KM>
 struct Isolator {
-  const Ctx* C;
+  const Ctx<KM>* C;
   U192 U;
   U192 cells[kMaxCells];
   int nc;
@@ -393,6 +429,7 @@ __device__ unsigned __int128 isqrt192(const U192& u) {
   return r;
 }
 
+template <int KM>
 __global__ void __launch_bounds__(kVerifyThreads) k_verify(VerifyArgs a) {
   pdl_wait();  // the sieve grid's survivors and header are complete from here on
   if (a.zero_block && blockIdx.x == 0) {  // the other result block, for the next single-range run
@@ -401,8 +438,8 @@ __global__ void __launch_bounds__(kVerifyThreads) k_verify(VerifyArgs a) {
   }
   ull n = a.hdr->n_surv;
   if (n > a.surv_cap) n = a.surv_cap;
-  Ctx C;
-  Isolator iso;
+  Ctx<KM> C;
+  Isolator<KM> iso;
   iso.C = &C;
   for (ull idx = blockIdx.x * (ull)blockDim.x + threadIdx.x; idx < n;
        idx += (ull)gridDim.x * blockDim.x) {
@@ -410,7 +447,10 @@ __global__ void __launch_bounds__(kVerifyThreads) k_verify(VerifyArgs a) {
     const uint32_t p32 = (uint32_t)(rec >> 32), q32 = (uint32_t)rec;  // relative to the range's base
     const uint32_t k = a.surv_range ? a.surv_range[idx] : 0u;
     const ull p = p32 + (a.base ? a.base[2 * (ull)k] : 0ull), q = q32 + (a.base ? a.base[2 * (ull)k + 1] : 0ull);
-    ctx_init(C, p, q);
+    if (!ctx_init(C, p, q)) {  // more moduli than this instantiation holds: never guess
+      atomicOr(&a.hdr->status, kStatusVerifyFail);
+      continue;
+    }
     const ull M = p > q ? p : q;
     const unsigned __int128 M2 = (unsigned __int128)M * M;  // < 2^80
     iso.U = umul128(M2 * 45u, M2);                           // 45 M^4 < 2^166
@@ -484,15 +524,9 @@ bool is_prime64(ull n) {
 std::mutex g_init_mu;
 bool g_inited[64];
 
-}  // namespace
-
-cudaError_t verify_init_device() {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lk(g_init_mu);
-  if (dev >= 0 && dev < 64 && g_inited[dev]) return cudaSuccess;
-  ModConst mods[kMaxMod];
-  ull ginv[kMaxMod][kMaxMod] = {};
+// The moduli: the kMaxMod largest primes below 2^62 (all above 2^61), with their
+// Montgomery constants, and the Garner inverses m_i^-1 mod m_j in Montgomery form.
+void host_moduli(ModConst mods[kMaxMod], ull ginv[kMaxMod][kMaxMod]) {
   ull cand = (1ull << 62) - 1;
   for (int j = 0; j < kMaxMod; ++j) {
     while (!is_prime64(cand)) cand -= 2;
@@ -516,15 +550,121 @@ cudaError_t verify_init_device() {
       const ull inv = powmod_h(mods[i].m % mj, mj - 2, mj);
       ginv[i][j] = (ull)(((u128)inv << 64) % mj);  // Montgomery form
     }
+}
+
+}  // namespace
+
+cudaError_t verify_init_device() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (dev >= 0 && dev < 64 && g_inited[dev]) return cudaSuccess;
+  ModConst mods[kMaxMod];
+  ull ginv[kMaxMod][kMaxMod] = {};
+  host_moduli(mods, ginv);
   cudaError_t e = cudaMemcpyToSymbol(c_mod, mods, sizeof(mods));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ginv, ginv, sizeof(ginv));
   if (e == cudaSuccess && dev >= 0 && dev < 64) g_inited[dev] = true;
   return e;
 }
 
+// The instantiation holding the moduli of the launch's largest p, q (max_bits; 0: any
+// 32-bit pair, or any pair below 2^40 when records carry bases).
+namespace {
+
+// Test probe of the modular arithmetic (op 0: a b mod m_j; op 1: a mod m_j; op 2: the
+// sign of the integer whose residues modulo m_0..m_{j-1} are a[i j .. i j + j - 1]).
+__global__ void k_probe_modarith(uint32_t op, uint32_t j, const ull* a, const ull* b, uint32_t n, ull* out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = 0;
+  if (op == 0) {
+    const ModConst M = c_mod[j];
+    out[i] = frommont(mmul(tomont(a[i], M), tomont(b[i], M), M), M);
+  } else if (op == 1) {
+    out[i] = red64(a[i], c_mod[j].m);
+  } else {
+    ull x[kMaxMod];
+    bool zero = true;
+    for (uint32_t k = 0; k < j; ++k) {
+      x[k] = tomont(a[(size_t)i * j + k], c_mod[k]);
+      zero &= x[k] == 0;
+    }
+    out[i] = zero ? 0ull : (ull)(long long)garner_sign<kMaxMod>(x, (int)j, c_mod, c_ginv);
+  }
+}
+
+}  // namespace
+
 cudaError_t launch_verify(const VerifyArgs& a, uint32_t blocks, cudaStream_t s, bool pdl) {
-  const cudaError_t e = launch_ex(k_verify, blocks, kVerifyThreads, 0, s, pdl, a);
+  const int bits = a.max_bits ? (int)a.max_bits : (a.base ? 40 : 32);
+  const int K = moduli_for_bits(bits);
+  cudaError_t e;
+  if (K <= 4) e = launch_ex(k_verify<4>, blocks, kVerifyThreads, 0, s, pdl, a);
+  else if (K <= 6) e = launch_ex(k_verify<6>, blocks, kVerifyThreads, 0, s, pdl, a);
+  else if (K <= 8) e = launch_ex(k_verify<8>, blocks, kVerifyThreads, 0, s, pdl, a);
+  else if (K <= 10) e = launch_ex(k_verify<10>, blocks, kVerifyThreads, 0, s, pdl, a);
+  else if (K <= 12) e = launch_ex(k_verify<12>, blocks, kVerifyThreads, 0, s, pdl, a);
+  else e = launch_ex(k_verify<kMaxMod>, blocks, kVerifyThreads, 0, s, pdl, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace cuboid
+
+// Probe of the root test's modular arithmetic for the tests: on the host (device = 0, the
+// same functions compiled for the host) or on the GPU (device = 1).  op 0: out[i] =
+// a[i] b[i] mod m_j by Montgomery products; op 1: out[i] = a[i] mod m_j; op 2: out[i] =
+// sign (0, 1 or 2^64 - 1 for -1) of the integer X with |X| < (prod m_k - 1) / 2 whose
+// residues modulo m_0 .. m_{j-1} are a[i j .. i j + j - 1] (Garner); op 3: out[k] = m_k for
+// k < 14 (n ignored).  Host buffers; synchronous.
+extern "C" int cuboid_probe_modarith(uint32_t op, uint32_t j, const uint64_t* a, const uint64_t* b, uint32_t n,
+                                     uint64_t* out, int device) {
+  using namespace cuboid;
+  if (!out || op > 3 || (op < 2 && j >= (uint32_t)kMaxMod) || (op == 2 && (j < 1 || j > (uint32_t)kMaxMod)) ||
+      (op < 3 && n && !a) || (op == 0 && n && !b))
+    return CUBOID_EINVAL;
+  ModConst mods[kMaxMod];
+  ull ginv[kMaxMod][kMaxMod] = {};
+  host_moduli(mods, ginv);
+  if (op == 3) {
+    for (int k = 0; k < kMaxMod; ++k) out[k] = mods[k].m;
+    return CUBOID_OK;
+  }
+  if (n == 0) return CUBOID_OK;
+  if (!device) {
+    for (uint32_t i = 0; i < n; ++i) {
+      if (op == 0) {
+        const ModConst& M = mods[j];
+        out[i] = frommont(mmul(tomont(a[i], M), tomont(b[i], M), M), M);
+      } else if (op == 1) {
+        out[i] = red64(a[i], mods[j].m);
+      } else {
+        ull x[kMaxMod];
+        bool zero = true;
+        for (uint32_t k = 0; k < j; ++k) {
+          x[k] = tomont(a[(size_t)i * j + k], mods[k]);
+          zero &= x[k] == 0;
+        }
+        out[i] = zero ? 0ull : (ull)(long long)garner_sign<kMaxMod>(x, (int)j, mods, ginv);
+      }
+    }
+    return CUBOID_OK;
+  }
+  cudaError_t e = verify_init_device();
+  const size_t na = op == 2 ? (size_t)n * j : n;
+  ull *d_a = nullptr, *d_b = nullptr, *d_out = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&d_a, na * sizeof(ull));
+  if (e == cudaSuccess) e = cudaMalloc(&d_b, n * sizeof(ull));
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, n * sizeof(ull));
+  if (e == cudaSuccess) e = cudaMemcpy(d_a, a, na * sizeof(ull), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && op == 0) e = cudaMemcpy(d_b, b, n * sizeof(ull), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_probe_modarith<<<(n + 255) / 256, 256>>>(op, j, d_a, d_b, n, d_out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, n * sizeof(ull), cudaMemcpyDeviceToHost);
+  cudaFree(d_a);
+  cudaFree(d_b);
+  cudaFree(d_out);
+  return status_from_cuda(e);
+}

@@ -152,3 +152,93 @@ def test_autotune_keeps_results(env, tmp_path):
         cb.cuboid_result_free(res)
     finally:
         cb.cuboid_tables_free(t)
+
+
+def test_overflowing_query_does_not_fail_its_batch(env):
+    """With the weak table of 13, most pairs survive.  Four queries of ~39k survivors keep
+    the server's streams busy while 6 queries of ~34k survivors, 12 small ones and one of
+    ~108k survivors queue up and are batched together: the batch's survivor buffer (2^16
+    records) overflows.  Every query whose records did not all fit runs again alone; the
+    others keep their results.  Each result equals the query sieved alone (with a large
+    buffer), except the one that overflows even alone: EOVERFLOW, with exact pair total
+    and counts."""
+    cb, stream = env
+    t = cb.cuboid_tables_build([13], 0, stream)
+    srv = cb.cuboid_server_create(t, 0, 256)
+    try:
+        occupy = [W.rect(1000 + 400 * i, 1299 + 400 * i, 5000, 5299) for i in range(4)]
+        medium = [W.rect(2000 + 300 * i, 2279 + 300 * i, 7000, 7279) for i in range(6)]
+        small = [W.rect(100 + 20 * i, 109 + 20 * i, 1000, 1099) for i in range(12)]
+        big = W.rect(10000, 10499, 20000, 20499)
+        queries = occupy + medium[:3] + small[:6] + [big] + medium[3:] + small[6:]
+        tickets = [cb.cuboid_server_submit(srv, q) for q in queries]
+        assert all(tk is not None for tk in tickets)
+        results = _wait(cb, srv, tickets, 1)
+        for q, (st, got) in zip(queries, results):
+            r = cb.cuboid_sieve(t, q["p_lo"], q["p_hi"], q["q_lo"], q["q_hi"], 0, stream)
+            assert cb.cuboid_result_wait(r) == cb.OK
+            want = cb.cuboid_result_get(r, 0, 1)
+            cb.cuboid_result_free(r)
+            if q is big:
+                assert st == cb.EOVERFLOW
+                assert got["n_pairs"] == want["n_pairs"] and got["counts"] == want["counts"]
+                assert len(want["survivors"]) > 1 << 16
+            else:
+                assert st == cb.OK, q
+                _same(got, want)
+        stats = cb.cuboid_server_stats(srv)
+        assert stats["retried"] >= 1
+        assert stats["finished"] == stats["admitted"] == len(queries)
+    finally:
+        assert cb.cuboid_server_destroy(srv, 60000) == cb.OK
+        cb.cuboid_tables_free(t)
+
+
+def test_replay_matches_polled_results(env, golden):
+    """The native load replay: every query finishes, its latency is positive, its pair
+    total is the stored oracle result's, and its result stays available to poll."""
+    cb, stream = env
+    primes = golden["primes"]
+    t = cb.cuboid_tables_build(primes, 0, stream)
+    srv = cb.cuboid_server_create(t, 0, 256)
+    try:
+        qs = golden["ranges"]
+        r = cb.cuboid_server_replay(srv, qs, [1e-4 * i for i in range(len(qs))], 60000)
+        assert all(st == cb.OK for st in r["status"]) and all(x > 0 for x in r["latency_s"])
+        assert r["npairs"] == [w["n_pairs"] for w in golden["results"]]
+        assert r["wall_s"] >= 1e-4 * (len(qs) - 1)
+        for tk, want in zip(r["tickets"], golden["results"]):
+            res = cb.cuboid_server_poll(srv, tk)
+            assert res is not None and cb.cuboid_result_wait(res) == cb.OK
+            _same(cb.cuboid_result_get(res, 0, len(primes)), want)
+            cb.cuboid_result_free(res)
+        with pytest.raises(Exception):
+            cb.cuboid_server_replay(srv, qs[:2], [1.0, 0.5], 1000)  # arrival times must not decrease
+    finally:
+        assert cb.cuboid_server_destroy(srv, 60000) == cb.OK
+        cb.cuboid_tables_free(t)
+
+
+def test_served_full_size_queries_vs_oracle(env):
+    """The 24 full-size serving queries (areas up to 2^26, p, q < 2^24) submitted together
+    to the server: each result equals the oracle's stored result."""
+    import gzip
+    cb, stream = env
+    with gzip.open(os.path.join(GOLDEN, "c5_full_queries.json.gz"), "rt") as f:
+        g = json.load(f)
+    n = len(g["primes"])
+    t = cb.cuboid_tables_build(g["primes"], cb.ORDER_BY_RATE, stream)
+    srv = cb.cuboid_server_create(t, 0, 256)
+    try:
+        tickets = [cb.cuboid_server_submit(srv, q) for q in g["ranges"]]
+        got = _wait(cb, srv, tickets, n)
+        for (st, a), want in zip(got, g["results"]):
+            c = [0] * n
+            for i, v in want["counts_nz"]:
+                c[i] = v
+            assert st == cb.OK
+            _same(a, {"n_pairs": want["n_pairs"], "counts": c, "survivors": want["survivors"],
+                      "roots": want["roots"]})
+    finally:
+        assert cb.cuboid_server_destroy(srv, 60000) == cb.OK
+        cb.cuboid_tables_free(t)
