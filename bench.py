@@ -742,13 +742,13 @@ def e2e_leg(cb, torch, spec, args, cold=False):
     return out
 
 
-def serving_leg(cb, torch, stream, args, rates=(1e2, 3e2, 1e3, 3e3, 1e4), beyond=(3e4, 1e5, 3e5, 1e6)):
+def serving_leg(cb, torch, stream, args, rates=(1e2, 3e2, 1e3, 3e3, 1e4), beyond=(3e4, 1e5, 3e5, 1e6, 3e6, 1e7)):
     """Poisson streams of range queries (area 2^U(10,26), p, q < 2^24, 128 primes) served
     by the continuous-batching loop.  Each offered rate runs for min(serving_seconds,
     serving_queries / rate) seconds of arrivals, replayed by the library's native load
     loop (cuboid_server_replay) so that the host language does not limit the offered
     load; latency = admission to result on the host, per query (p50/p99).  The rates past
-    1e4/s look for saturation: the first offered rate whose achieved query rate falls below
+    1e4/s (up to 1e7/s) look for saturation: the first offered rate whose achieved query rate falls below
     90 % of it.  Served-in-mix = run-alone (pair totals, counts, survivors and roots) on a
     seeded 1 % of the queries of every rate."""
     import random

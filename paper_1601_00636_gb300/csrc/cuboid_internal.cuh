@@ -209,6 +209,8 @@ struct SieveArgs {
   uint32_t n_hot;               // hot primes (0, 2, 4, 5, 6 or 8): the first n_hot of the effective order
   uint32_t hot_r[8], hot_magic[8], hot_off[8], hot_W[8];
   uint32_t hot_step[8];          // (128 row_lanes) mod r: a lane's stride between pairs of words
+  uint32_t hot_step_m[8];        // hot_step - r (mod 2^32)
+  uint32_t one = 1;              // the multiplier of the adds the sieve issues on the FMA pipe
   uint32_t row_lanes;            // lanes per row (8, 16, 32)
   uint32_t stage_spins;          // polls of the staging barrier before a time-out
   // Single-range launch without a plan kernel (self_plan = 1): every CTA plans the range

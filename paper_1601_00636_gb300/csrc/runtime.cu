@@ -157,6 +157,7 @@ void fill_hot(SieveArgs& a, const cuboid_tables* t, const LaunchShape& L) {
     a.hot_off[h] = pi.off;
     a.hot_W[h] = pi.W;
     a.hot_step[h] = (128u * L.row_lanes) % pi.r;  // a lane's stride between pairs of words
+    a.hot_step_m[h] = a.hot_step[h] - pi.r;
   }
 }
 

@@ -29,8 +29,11 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr unsigned long long FULL64 = ~0ull;
 constexpr uint32_t kNoRange = 0xFFFFFFFFu;
 constexpr uint32_t kFlushTiles = 256;       // per-warp uint32 counters are flushed at least this often
-constexpr uint32_t kQueue = 64;             // per-warp queue of words that outlive the hot primes
+constexpr uint32_t kQueue = 96;             // per-warp queue of words that outlive the hot primes (below 32
+                                            // after a drain, plus up to 64 from one pair of words per lane)
 constexpr int kFacRegs = 4;                 // odd factors whose per-lane offsets sit in registers
+constexpr uint32_t kMobiusIters = 8;        // subtiles whose lanes take this many iterations count their
+                                            // pairs by Moebius inversion instead of per-word popcounts
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
   for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
@@ -48,6 +51,7 @@ struct WarpState {
   uint32_t imax;            // deepest prime index reached since the last flush
   uint32_t tiles_since_flush;
   unsigned long long npairs;
+  unsigned long long qbits;  // alive pairs of the words queued after the hot primes (since the last fold)
 };
 
 __device__ __forceinline__ void flush_counts(WarpState& ws, uint32_t* wcnt, const SieveArgs& a,
@@ -86,6 +90,40 @@ __device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity, 
   return false;
 }
 
+// Integer adds and address arithmetic issued on the FMA pipe: x * one + y with one == 1
+// at run time (the compiler cannot fold the multiply, so the add does not take a slot of
+// the ALU pipe, which the shifts, logic ops and minima keep busy).
+__device__ __forceinline__ uint32_t fma_add(uint32_t x, uint32_t y, uint32_t one) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one), "r"(y));
+  return d;
+}
+__device__ __forceinline__ uint32_t fma_sub(uint32_t x, uint32_t y, uint32_t one) {  // x - y
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(y), "r"(0u - one), "r"(x));
+  return d;
+}
+__device__ __forceinline__ uint32_t fma_mad(uint32_t x, uint32_t k, uint32_t y) {  // x k + y
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(k), "r"(y));
+  return d;
+}
+__device__ __forceinline__ uint32_t mulhi_fma(uint32_t x, uint32_t k) {  // (x k) >> 32
+  uint32_t d;
+  asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(x), "r"(k));
+  return d;
+}
+// Five consecutive 32-bit words of shared memory from byte address ad.  The staged
+// tables do not change while the kernel sieves, so the loads are pure (no volatile, no
+// memory clobber) and the compiler may move them ahead of the arithmetic that uses them.
+__device__ __forceinline__ void lds5(uint32_t ad, uint32_t& w0, uint32_t& w1, uint32_t& w2, uint32_t& w3,
+                                     uint32_t& w4) {
+  asm("ld.shared.u32 %0, [%5];\n ld.shared.u32 %1, [%5+4];\n ld.shared.u32 %2, [%5+8];\n"
+      " ld.shared.u32 %3, [%5+12];\n ld.shared.u32 %4, [%5+16];"
+      : "=r"(w0), "=r"(w1), "=r"(w2), "=r"(w3), "=r"(w4)
+      : "r"(ad));
+}
+
 // n mod r for any 32-bit n, with magic = floor(2^32 / r): n - floor(n*magic/2^32) r is
 // n mod r or n mod r + r, and the unsigned minimum with itself minus r picks the residue.
 __device__ __forceinline__ uint32_t mod_min(uint32_t n, uint32_t r, uint32_t magic) {
@@ -105,6 +143,9 @@ __device__ __forceinline__ void cold_batch(const SieveArgs& a, const PrimeInfo* 
   const uint4 e = lane < cnt ? q[lane] : make_uint4(0u, 0u, 0u, 0u);
   const uint32_t x = e.x, y0 = e.y;
   uint32_t al = e.z, ah = e.w;
+  // the pairs these words carry out of the hot primes: the last hot prime's count is the
+  // pairs alive before it minus these (see fold)
+  ws.qbits += __reduce_add_sync(FULL, __popc(al) + __popc(ah));
   const uint32_t n = a.n_primes;
   uint32_t i = first;
   for (; i < n; ++i) {
@@ -184,12 +225,15 @@ __device__ __forceinline__ void drain(const SieveArgs& a, const PrimeInfo* s_inf
     const uint32_t cnt = qn < 32 ? qn : 32;
     cold_batch<kSteps, kWide>(a, s_info, s_tab, s_ybr, wcnt, q, cnt, first, rows_q, range, lane, ws, st_wsteps,
                               st_warpsteps);
-    const uint32_t rest = qn - cnt;
-    uint4 e = make_uint4(0u, 0u, 0u, 0u);
-    const bool mv = lane < rest && CUBOID_IDX_OK(32 + lane < kQueue, a.hdr, 7u);
-    if (mv) e = q[32 + lane];
+    const uint32_t rest = qn - cnt;  // below 64: entries 32 .. 32 + rest move to the front
+    uint4 e0 = make_uint4(0u, 0u, 0u, 0u), e1 = e0;
+    const bool mv0 = lane < rest && CUBOID_IDX_OK(32 + lane < kQueue, a.hdr, 7u);
+    const bool mv1 = lane + 32 < rest && CUBOID_IDX_OK(64 + lane < kQueue, a.hdr, 7u);
+    if (mv0) e0 = q[32 + lane];
+    if (mv1) e1 = q[64 + lane];
     __syncwarp();
-    if (mv) q[lane] = e;
+    if (mv0) q[lane] = e0;
+    if (mv1) q[32 + lane] = e1;
     __syncwarp();
     qn = rest;
   }
@@ -312,7 +356,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   const uint32_t count = a.self_plan ? 1u : (a.range_count == kNoRange ? a.hdr->n_ranges : a.range_count);
   const unsigned long long total = a.self_plan ? s_self_total : a.hdr->total_tiles;
 
-  WarpState ws{kNoRange, 0, 0, 0};
+  WarpState ws{kNoRange, 0, 0, 0, 0};
   unsigned long long st_words = 0, st_wsteps = 0, st_warpsteps = 0, st_tiles = 0;
   uint32_t qn = 0;       // queued words (warp-uniform), all of range ws.cur_range
   bool q_rows = false;   // orientation of the queued words
@@ -326,15 +370,22 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
 #pragma unroll
   for (int h = 0; h < (K > 0 ? K : 1); ++h) hs[h] = 0;
   uint32_t tile_pairs = 0;
+  // Call with the queue drained: the pairs alive after the last hot prime are then those
+  // counted into ws.qbits, so its per-lane sum is not kept in the word loop.
   auto fold = [&]() {
     uint32_t before = tile_pairs;
 #pragma unroll
-    for (int h = 0; h < K; ++h) {
+    for (int h = 0; h + 1 < K; ++h) {
       const uint32_t c = __reduce_add_sync(FULL, before - hs[h]);
       if (lane == 0 && c) wcnt[h] += c;
       before = hs[h];
       hs[h] = 0;
     }
+    if constexpr (K > 0) {
+      const uint32_t c = (uint32_t)(__reduce_add_sync(FULL, before) - ws.qbits);
+      if (lane == 0 && c) wcnt[K - 1] += c;
+    }
+    ws.qbits = 0;
     ws.npairs += __reduce_add_sync(FULL, tile_pairs);
     tile_pairs = 0;
     __syncwarp();
@@ -364,9 +415,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     const TilePlan P = count == 1 ? P1 : a.plan[k];
     const unsigned long long tbeg = (k == a.range_first) ? 0ull : a.plan[k - 1].tile_end;
     if (k != ws.cur_range || ws.tiles_since_flush >= kFlushTiles) {
-      fold();
       drain<kSteps, kWide>(a, s_info, s_tab, s_ybr, wcnt, s_queue, qn, K, q_rows, ws.cur_range, lane, ws,
                            st_wsteps, st_warpsteps, true);
+      fold();
       flush_counts(ws, wcnt, a, lane);
       ws.cur_range = k;
     }
@@ -434,6 +485,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     // prime power out of the cofactor through a product over the group.
     uint32_t nfo = 0;  // uniform in the group
     bool has2 = false;
+    uint32_t big = 1;  // a prime factor above 2^31 left out of the masks (x itself), or 1
     {
       uint32_t m = x;
       if ((m & 1u) == 0) {
@@ -487,7 +539,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         m *= inv;  // exact: pw divides m
         nfo += __popc(bal);
       }
-      if (live && m > 1) {  // a prime: above every trial prime tested, or below 9 if no batch ran
+      // the cofactor is a prime: above every trial prime tested, or below 9 if no batch ran.
+      // A prime factor above 2^31 is x itself, whose only multiple below 2^32 is the
+      // diagonal y = x (handled with the range edges), so 32-bit ranges leave it out.
+      if (live && m > 1 && (kWide || m <= 0x80000000u)) {
         if (gl == 0 && CUBOID_IDX_OK(nfo < kMaxFactors, a.hdr, 5u)) {
           const uint32_t mag = 0xFFFFFFFFu / m;
           s_fac[nfo] = make_uint4(m, mod_min(kStride, m, mag), m < kPeriodicBelow ? s_foff[m] : kBitTab,
@@ -496,6 +551,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           if constexpr (kWide) s_fyb[nfo] = (uint32_t)(a.y_base % m);
         }
         ++nfo;
+      } else if (live && m > 1) {
+        big = m;
       }
       // inert entries up to kFacRegs: offset 128 that never moves, empty mask
       if (gl < (uint32_t)kFacRegs && gl >= nfo) s_fac[gl] = make_uint4(1u, 0u, kBitTab, 128u);
@@ -520,12 +577,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
       }
     }
 
-    // ---- row offsets of the hot primes
+    // ---- row offsets of the hot primes (word index, and shared byte address)
     uint32_t rb[K > 0 ? K : 1];
+    uint32_t rb4[K > 0 ? K : 1];
     uint32_t sh[K > 0 ? K : 1];  // y0 mod r of the lane's current word, advanced per slot
+    const uint32_t tab_addr = (uint32_t)__cvta_generic_to_shared(s_tab);
 #pragma unroll
     for (int h = 0; h < K; ++h) {
       rb[h] = a.hot_off[h] + mod_min(x, a.hot_r[h], a.hot_magic[h]) * a.hot_W[h];
+      rb4[h] = tab_addr + 4u * rb[h];
       uint32_t s0 = mod_min(y0f, a.hot_r[h], a.hot_magic[h]);
       if constexpr (kWide) {
         s0 += s_ybr[h];
@@ -534,41 +594,87 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
       sh[h] = s0;
     }
 
-    const uint32_t emask = has2 ? 0xAAAAAAAAu : FULL;  // x even: y0 is even, so even y sit at even bits
     const uint32_t npairs_sub = live ? (wend - wbeg) / 2 + 1 : 0u;  // pairs of words of the subtile
     const uint32_t nit = (npairs_sub + G - 1) / G;                 // iterations of this lane's group
     const uint32_t maxit = G == 32 ? nit : __reduce_max_sync(FULL, nit);
-    // one word's range edges and diagonal on top of its coprimality mask
-    auto finish_word = [&](uint32_t w, bool on, uint32_t ml, uint32_t mh, uint32_t& al, uint32_t& ah) {
-      al = 0;
-      ah = 0;
-      if (on) {
-        unsigned long long rm = FULL64;
-        if (w == wlo) rm &= lo_mask;
-        if (w == whi) rm &= hi_mask;
-        const uint32_t rml = (uint32_t)rm, rmh = (uint32_t)(rm >> 32);
-        al = rml & emask & ~ml;
-        ah = rmh & emask & ~mh;
-        if (w == dword) {
-          al &= ~dbit_lo;
-          ah &= ~dbit_hi;
-          if (diag) {
-            al |= dbit_lo & rml;
-            ah |= dbit_hi & rmh;
-          }
+    const uint32_t one = a.one;  // 1 at run time: x * one + y issues on the FMA pipe
+    // Pairs of the subtile when its lanes take many iterations (instead of a popcount per
+    // word): Moebius inversion over the prime factors of x,
+    //   #{y in [Y0, Y1] : gcd(x, y) = 1} = sum over sets S of them of (-1)^|S| (floor(Y1 / d)
+    //   - floor((Y0 - 1) / d)), d the product of S,
+    // then the diagonal y = x (coprime only for x = 1; the range flag admits it).  Lane gl
+    // of the group takes every G-th set; the warp's sums add up the lanes' parts.
+    const bool mob = !kWide && maxit >= kMobiusIters;  // uniform in the warp
+    if (mob && live) {
+      const uint32_t Y0 = (uint32_t)max((unsigned long long)ylo, (unsigned long long)wbeg << 6);
+      const uint32_t Y1 = (uint32_t)min(yhi, ((unsigned long long)wend << 6) + 63);
+      const uint32_t np = nfo + (has2 ? 1u : 0u) + (big > 1 ? 1u : 0u);
+      uint32_t part = 0;  // modulo 2^32: the warp's total is what counts
+      for (uint32_t set = gl; set < (1u << np); set += G) {
+        unsigned long long d = 1;
+        uint32_t sign = 0;
+        for (uint32_t b = 0; b < np && d <= Y1; ++b) {
+          if (!((set >> b) & 1u)) continue;
+          const uint32_t f = b < nfo ? s_fac[b].x : (b == nfo && has2 ? 2u : big);
+          d *= f;
+          sign ^= 1u;
         }
-        tile_pairs += __popc(al) + __popc(ah);
-        if (kSteps) st_words += (al | ah) ? 1 : 0;
+        if (d > Y1) continue;
+        const uint32_t t = Y1 / (uint32_t)d - (Y0 - 1) / (uint32_t)d;
+        part += sign ? 0u - t : t;
+      }
+      if (gl == 0 && x >= Y0 && x <= Y1) {
+        if (x == 1 && !diag) part -= 1;
+        if (x > 1 && diag) part += 1;
+      }
+      tile_pairs += part;
+    }
+    // x even: y0 is even, so the even y (excluded) sit at the even bits
+    const uint32_t even_bits = has2 ? 0x55555555u : 0u;
+    // Interior pairs of words (neither word on a range edge, both in the subtile) have
+    // their first word in [int_lo, int_lo + int_span]; the others take the edge path,
+    // as do the pairs holding the diagonal word.
+    const long long int_hi = (long long)(wend < whi ? wend + 1 : whi) - 2;  // last interior first word
+    const long long int_lo = (long long)wlo + 1;
+    // no interior: base 2^32 - 1 and span 0 make every pair an edge (word indices < 2^26)
+    const bool has_interior = live && int_hi >= int_lo;
+    const uint32_t int_span = has_interior ? (uint32_t)(int_hi - int_lo) : 0u;
+    const uint32_t int_base = has_interior ? (uint32_t)int_lo : 0xFFFFFFFFu;
+    const bool diag_in = dword >= wbeg && dword <= wend;
+    // one word's exclusions beyond coprimality: bits outside the range, the diagonal
+    // (unless the range admits it: then it is kept whatever the masks say)
+    auto edge_word = [&](uint32_t w, bool on, uint32_t& ml, uint32_t& mh) {
+      if (!on) {
+        ml = mh = FULL;
+        return;
+      }
+      unsigned long long rm = FULL64;
+      if (w == wlo) rm &= lo_mask;
+      if (w == whi) rm &= hi_mask;
+      const uint32_t rml = (uint32_t)rm, rmh = (uint32_t)(rm >> 32);
+      ml |= ~rml;
+      mh |= ~rmh;
+      if (w == dword) {
+        ml |= dbit_lo;
+        mh |= dbit_hi;
+        if (diag) {
+          ml &= ~(dbit_lo & rml);
+          mh &= ~(dbit_hi & rmh);
+        }
       }
     };
-    // queue the lanes' words still alive and finish full batches of 32 through the rest
-    // of the primes
-    auto enqueue = [&](uint32_t al, uint32_t ah, uint32_t y0) {
-      const uint32_t bal = __ballot_sync(FULL, (al | ah) != 0u);
-      if (bal) {
-        const uint32_t slot = qn + __popc(bal & lanemask_lt);
-        if ((al | ah) && CUBOID_IDX_OK(slot < kQueue, a.hdr, 6u)) s_queue[slot] = make_uint4(x, y0, al, ah);
-        qn += __popc(bal);
+    // queue the words of the lanes' pairs still alive (the warp's A words, then its B
+    // words, in lane order) and finish full batches of 32 through the rest of the primes
+    auto enqueue2 = [&](uint32_t alA, uint32_t ahA, uint32_t alB, uint32_t ahB, uint32_t y0) {
+      const bool liveA = (alA | ahA) != 0u, liveB = (alB | ahB) != 0u;
+      const uint32_t balA = __ballot_sync(FULL, liveA), balB = __ballot_sync(FULL, liveB);
+      if (balA | balB) {
+        const uint32_t nA = __popc(balA);
+        const uint32_t slotA = qn + __popc(balA & lanemask_lt);
+        const uint32_t slotB = qn + nA + __popc(balB & lanemask_lt);
+        if (liveA && CUBOID_IDX_OK(slotA < kQueue, a.hdr, 6u)) s_queue[slotA] = make_uint4(x, y0, alA, ahA);
+        if (liveB && CUBOID_IDX_OK(slotB < kQueue, a.hdr, 6u)) s_queue[slotB] = make_uint4(x, y0 + 64u, alB, ahB);
+        qn += nA + __popc(balB);
         __syncwarp();
         drain<kSteps, kWide>(a, s_info, s_tab, s_ybr, wcnt, s_queue, qn, K, rows_q, k, lane, ws, st_wsteps,
                              st_warpsteps, false);
@@ -578,20 +684,26 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     for (uint32_t j = 0; j < maxit; ++j, wb += 2 * G) {
       const uint32_t wA = wb, wB = wb + 1;  // the lane's pair of adjacent words
       const bool onA = j < nit && wA <= wend, onB = j < nit && wB <= wend;
-      // coprimality masks of both words at once: 128-bit masks from the image
-      uint4 m = make_uint4(0u, 0u, 0u, 0u);
+      // bits to exclude: y sharing a prime factor with x (128-bit masks from the image for
+      // both words at once), even y for even x, then the range edges and the diagonal
+      uint4 m = make_uint4(even_bits, even_bits, even_bits, even_bits);
       if (onA) {
 #pragma unroll
         for (int i = 0; i < kFacRegs; ++i) {  // inert entries give an empty mask
+          if (G == 32 && (uint32_t)i >= nfo) break;  // whole-warp rows: nfo is the warp's
           const uint4 fc = s_fac[i];          // {f, (128 G) mod f, table base, cap}
-          const uint32_t mi = fc.z + min(tf[i], fc.w);
+          const uint32_t mi = fma_add(fc.z, min(tf[i], fc.w), one);
           const uint4 mk = CUBOID_IDX_OK(mi < kMaskTab, a.hdr, 4u) ? s_mtab[mi] : make_uint4(0u, 0u, 0u, 0u);
           m.x |= mk.x;
           m.y |= mk.y;
           m.z |= mk.z;
           m.w |= mk.w;
-          // the lane's next pair starts 128 G further on: t <- (t - 128 G) mod f
-          tf[i] = tf[i] >= fc.y ? tf[i] - fc.y : tf[i] - fc.y + fc.x;
+          // the lane's next pair starts 128 G further on: t <- (t - 128 G) mod f, the
+          // smaller of t - y (wraps when t < y) and t - y + f (f <= 2^31, so no wrap)
+          if constexpr (kWide)  // a factor above 2^31 (x itself) has multiples 2x, 3x, ... here
+            tf[i] = tf[i] >= fc.y ? tf[i] - fc.y : tf[i] - fc.y + fc.x;
+          else
+            tf[i] = min(fma_add(tf[i], 0u - fc.y, one), fma_add(tf[i], fc.x - fc.y, one));
         }
         for (uint32_t i = kFacRegs; i < nfo; ++i) {
           const uint4 fc = s_fac[i];
@@ -609,45 +721,53 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           m.w |= mk.w;
         }
       }
-      uint32_t alA, ahA, alB, ahB;
-      finish_word(wA, onA, m.x, m.y, alA, ahA);
-      finish_word(wB, onB, m.z, m.w, alB, ahB);
+      // (a pair with a word outside the subtile, or of an idle group, is an edge pair too)
+      if (!onB || fma_add(wA, 0u - int_base, one) > int_span || (diag_in && (wA == dword || wB == dword))) {
+        edge_word(wA, onA, m.x, m.y);
+        edge_word(wB, onB, m.z, m.w);
+      }
+      uint32_t alA = ~m.x, ahA = ~m.y, alB = ~m.z, ahB = ~m.w;
+      if (!mob) {  // pairs of this pair of words: 128 minus the excluded bits
+        tile_pairs = fma_add(tile_pairs, 128u, one);
+        tile_pairs = fma_sub(tile_pairs, __popc(m.x), one);
+        tile_pairs = fma_sub(tile_pairs, __popc(m.y), one);
+        tile_pairs = fma_sub(tile_pairs, __popc(m.z), one);
+        tile_pairs = fma_sub(tile_pairs, __popc(m.w), one);
+      }
+      if (kSteps) st_words += ((alA | ahA) ? 1 : 0) + ((alB | ahB) ? 1 : 0);
       // hot primes: no early-exit test; one 128-bit window serves both words
 #pragma unroll
       for (int h = 0; h < K; ++h) {
         if (kSteps) st_wsteps += ((alA | ahA) ? 1 : 0) + ((alB | ahB) ? 1 : 0);
         const uint32_t s = sh[h];
-        const uint32_t sn = s + a.hot_step[h];  // next pair: + (128 G) mod r, below 2r
-        sh[h] = min(sn, sn - a.hot_r[h]);
-        const uint32_t* tp = s_tab + rb[h] + (s >> 5);
+        // next pair: + (128 G) mod r; the smaller of s + step and s + step - r (which
+        // wraps when s + step < r) is the residue
+        sh[h] = min(fma_add(s, a.hot_step[h], one), fma_add(s, a.hot_step_m[h], one));
+        // shared byte address of word s / 32 of the row (s >> 5 by a multiply-high)
+        const uint32_t ad = fma_mad(mulhi_fma(s, 1u << 27), 4u, rb4[h]);
         uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0;
         // the window stays inside row (x mod r): s < r, its last word before the row's end
         if (CUBOID_IDX_OK(s < a.hot_r[h] && (s >> 5) + 4 < a.hot_W[h] && rb[h] + (s >> 5) + 4 < a.smem_words,
-                          a.hdr, 1u)) {
-          w0 = tp[0];
-          w1 = tp[1];
-          w2 = tp[2];
-          w3 = tp[3];
-          w4 = tp[4];
-        }
+                          a.hdr, 1u))
+          lds5(ad, w0, w1, w2, w3, w4);
         alA &= ~__funnelshift_r(w0, w1, s);  // the window of u_r(x mod r, y0 mod r ...)
         ahA &= ~__funnelshift_r(w1, w2, s);
         alB &= ~__funnelshift_r(w2, w3, s);
         ahB &= ~__funnelshift_r(w3, w4, s);
-        hs[h] += __popc(alA) + __popc(ahA) + __popc(alB) + __popc(ahB);
+        if (h + 1 < K)  // the last hot prime's count comes from the queued words
+          hs[h] += (__popc(alA) + __popc(ahA)) + (__popc(alB) + __popc(ahB));
       }
       if (kSteps) st_warpsteps += 2 * K;
-      enqueue(alA, ahA, wA << 6);
-      enqueue(alB, ahB, wB << 6);
+      enqueue2(alA, ahA, alB, ahB, wA << 6);
     }
     if constexpr (K > 0) {
       if ((uint32_t)(K - 1) > ws.imax) ws.imax = (uint32_t)(K - 1);
     }
     next = __shfl_sync(FULL, next, 0);
   }
-  fold();
   drain<kSteps, kWide>(a, s_info, s_tab, s_ybr, wcnt, s_queue, qn, K, q_rows, ws.cur_range, lane, ws, st_wsteps,
                        st_warpsteps, true);
+  fold();
   flush_counts(ws, wcnt, a, lane);
   if (kSteps) {
     const unsigned long long w = warp_sum_u64(st_words), s = warp_sum_u64(st_wsteps);
