@@ -242,7 +242,8 @@ __device__ __forceinline__ void drain(const SieveArgs& a, const PrimeInfo* s_inf
 // K: number of "hot" primes (the first K of the effective order, all resident in shared
 // memory).
 // kMaxThreads: 1024 keeps every kernel at <= 64 registers (two 512-thread CTAs per SM);
-// 512 lets a single 512-thread CTA per SM use up to 128 registers.
+// 640 allows 96 (20 warps per SM, e.g. two 320-thread CTAs); 512 lets 512 threads per SM
+// use up to 128 registers.
 // G: lanes per row.  A warp takes one tile = 32 / G consecutive subtiles of a range (a
 // subtile is one row and one chunk of its 64-value words); each group of G lanes sieves
 // one subtile, each lane a pair of adjacent words at a time, lanes on pairs G apart.  G = 32 is one subtile per warp; smaller groups
@@ -802,6 +803,9 @@ cudaError_t set_attr_all(size_t bytes) {
   cudaError_t e = set_attr_g<S, 1024, 32, false>(bytes);
   if (e == cudaSuccess) e = set_attr_g<S, 512, 32, false>(bytes);
   if constexpr (!S) {
+    if (e == cudaSuccess) e = set_attr_g<S, 640, 32, false>(bytes);
+    if (e == cudaSuccess) e = set_attr_g<S, 640, 16, false>(bytes);
+    if (e == cudaSuccess) e = set_attr_g<S, 640, 8, false>(bytes);
     if (e == cudaSuccess) e = set_attr_g<S, 1024, 16, false>(bytes);
     if (e == cudaSuccess) e = set_attr_g<S, 512, 16, false>(bytes);
     if (e == cudaSuccess) e = set_attr_g<S, 1024, 8, false>(bytes);
@@ -825,8 +829,10 @@ cudaError_t launch_g(const SieveArgs& a, uint32_t blocks, uint32_t threads, size
 
 template <bool S, int M>
 cudaError_t launch_m(const SieveArgs& a, uint32_t blocks, uint32_t threads, size_t smem, cudaStream_t s, bool pdl) {
-  if constexpr (!S) {
+  if constexpr (!S && M != 640) {  // 64-bit pieces: the 512- and 1024-thread builds
     if (a.y_base) return launch_g<S, M, 32, true>(a, blocks, threads, smem, s, pdl);
+  }
+  if constexpr (!S) {
     if (a.row_lanes == 8) return launch_g<S, M, 8, false>(a, blocks, threads, smem, s, pdl);
     if (a.row_lanes == 16) return launch_g<S, M, 16, false>(a, blocks, threads, smem, s, pdl);
   }
@@ -838,6 +844,9 @@ template <bool S>
 cudaError_t launch_k(const SieveArgs& a, uint32_t blocks, uint32_t threads, uint32_t per_sm, size_t smem,
                      cudaStream_t s, bool pdl) {
   if (threads * per_sm <= 512) return launch_m<S, 512>(a, blocks, threads, smem, s, pdl);
+  if constexpr (!S) {
+    if (threads * per_sm <= 640 && !a.y_base) return launch_m<S, 640>(a, blocks, threads, smem, s, pdl);
+  }
   return launch_m<S, 1024>(a, blocks, threads, smem, s, pdl);
 }
 

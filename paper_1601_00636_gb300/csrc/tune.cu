@@ -6,7 +6,8 @@
 // survivor/root totals must equal the first candidate's (the arithmetic never depends
 // on the shape); a mismatch is reported as CUBOID_EVERIFY.  The winner is set on the
 // tables and, with a cache path, remembered in a text file keyed by the device name,
-// the prime list (in its effective order), the ranges and the mode.
+// the revision of the sieve kernel, the prime list (in its effective order), the ranges
+// and the mode.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -48,7 +49,7 @@ std::string cache_key(const cuboid_tables* t, const cuboid_range* ranges, uint32
   std::string name(prop.name);
   for (char& c : name)
     if (c == ' ') c = '_';
-  snprintf(buf, sizeof(buf), "%s|%016llx|%016llx|%u|%u", name.c_str(), (unsigned long long)hp,
+  snprintf(buf, sizeof(buf), "%s|r%u|%016llx|%016llx|%u|%u", name.c_str(), kSieveRevision, (unsigned long long)hp,
            (unsigned long long)hr, n, mode);
   return buf;
 }
@@ -157,7 +158,7 @@ extern "C" int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uin
   st = measure(cur, &cur_ms);
   const uint32_t hots[] = {2, 4, 5, 6};
   const uint32_t tpws[] = {1, 2, 3, 4, 6, 8, 12, 16};
-  const uint32_t thr[] = {256, 512};
+  const uint32_t thr[] = {256, 320, 512};
   const uint32_t ctas[] = {1, 2, 4};
   const uint32_t smemp[] = {0, 8, 16, 32};
   const uint32_t lanes[] = {8, 16, 32};
@@ -186,7 +187,7 @@ extern "C" int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uin
         c.tiles_per_warp = v;
       }, tpws, 8);
     }
-    try_dim([](cuboid_tuning& c, uint32_t v) { c.block_threads = v; }, thr, 2);
+    try_dim([](cuboid_tuning& c, uint32_t v) { c.block_threads = v; }, thr, 3);
     try_dim([](cuboid_tuning& c, uint32_t v) { c.ctas_per_sm = v; }, ctas, 3);
     try_dim([](cuboid_tuning& c, uint32_t v) { c.smem_primes = v; }, smemp, 4);
   }

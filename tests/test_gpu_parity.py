@@ -309,7 +309,9 @@ TUNINGS = [dict(), dict(block_threads=256, ctas_per_sm=1), dict(block_threads=10
            dict(hot_primes=6, smem_primes=3), dict(row_lanes=8), dict(row_lanes=16),
            dict(row_lanes=8, tiles_per_warp=1, block_threads=512, ctas_per_sm=1, hot_primes=5),
            dict(row_lanes=16, tiles_per_warp=64, ctas_per_sm=4, block_threads=128, hot_primes=0),
-           dict(row_lanes=8, block_threads=1024, ctas_per_sm=1, hot_primes=6)]
+           dict(row_lanes=8, block_threads=1024, ctas_per_sm=1, hot_primes=6),
+           dict(block_threads=320, ctas_per_sm=2), dict(block_threads=640, ctas_per_sm=1, row_lanes=8),
+           dict(block_threads=320, ctas_per_sm=2, row_lanes=16, hot_primes=5, tiles_per_warp=1)]
 
 
 @pytest.mark.parametrize("tune", TUNINGS)
