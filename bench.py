@@ -469,13 +469,9 @@ def measure(cb, torch, dist, stream, flush, spec, args, world, rank, tables=None
         e1.record(stream)
     torch.cuda.synchronize()
     table_ms = e0.elapsed_time(e1)
-    # kernel shape picked by the autotuner (outside the timed region; the 2^20 triangle is
-    # tuned on its 4097 longest rows, a full pass takes ~40 ms)
-    tune_ranges = [rng]
-    if spec["side"] >= (1 << 20) and mode == cb.MODE_BATCHED:
-        top = max(rng["p_hi"], 4097)
-        tune_ranges = [W.rect(top - 4096, top, 1, top - 1, q_lt_p=True)]
-    tune, _ = cb.cuboid_autotune(t, tune_ranges, mode, stream, _tune_cache())
+    # kernel shape picked by the autotuner on this very workload (outside the timed region;
+    # a few seconds for the 2^20 triangle, cached)
+    tune, _ = cb.cuboid_autotune(t, [rng], mode, stream, _tune_cache())
     res = cb.cuboid_result_create(t, 1)
     arr = cb.ranges_array([rng])
     dev_ranges = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to("cuda")
@@ -691,11 +687,7 @@ def e2e_leg(cb, torch, spec, args, cold=False):
     s = torch.cuda.Stream()
     k = max(5, min(args.steps, 20))
     t = cb.cuboid_tables_build(primes, cb.ORDER_BY_RATE, s)
-    tune_ranges = [rng]
-    if spec["side"] >= (1 << 20) and mode == cb.MODE_BATCHED:
-        top = max(rng["p_hi"], 4097)
-        tune_ranges = [W.rect(top - 4096, top, 1, top - 1, q_lt_p=True)]
-    cb.cuboid_autotune(t, tune_ranges, mode, s, _tune_cache())
+    cb.cuboid_autotune(t, [rng], mode, s, _tune_cache())
     res = cb.cuboid_result_create(t, 1)
     arr = cb.ranges_array([rng])
     times, n_pairs, ok = [], 0, True

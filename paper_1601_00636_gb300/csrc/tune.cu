@@ -1,8 +1,8 @@
 // K6: autotuner of the sieve kernel shape.
 //
-// Coordinate descent over the kernel-shape knobs (hot primes, tiles per warp, threads per
-// CTA, CTAs per SM, primes staged in shared memory, lanes per row), timing each candidate on the
-// caller's own ranges with CUDA events.  Every candidate's counts, pair totals and
+// A search over the kernel-shape knobs, timing each candidate on the caller's own ranges
+// with CUDA events: hot primes, then lanes per row x CTA shape x tiles per warp as one
+// grid, then primes staged in shared memory, then hot primes again.  Every candidate's counts, pair totals and
 // survivor/root totals must equal the first candidate's (the arithmetic never depends
 // on the shape); a mismatch is reported as CUBOID_EVERIFY.  The winner is set on the
 // tables and, with a cache path, remembered in a text file keyed by the device name,
@@ -130,7 +130,7 @@ extern "C" int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uin
   auto measure = [&](const cuboid_tuning& tu, float* out_ms) -> int {
     t->tuning = tu;
     float best = 1e30f;
-    for (int rep = 0; rep < 4; ++rep) {
+    for (int rep = 0; rep < 3; ++rep) {  // the first run warms up
       cudaEventRecord(e0, s);
       int r2 = sieve_into(res, ranges, n, mode, s, false, false);
       if (r2 != CUBOID_OK) return r2;
@@ -157,40 +157,49 @@ extern "C" int cuboid_autotune(cuboid_tables* t, const cuboid_range* ranges, uin
   float cur_ms = 0.f;
   st = measure(cur, &cur_ms);
   const uint32_t hots[] = {2, 4, 5, 6};
-  const uint32_t tpws[] = {1, 2, 3, 4, 6, 8, 12, 16};
-  const uint32_t thr[] = {256, 320, 512};
-  const uint32_t ctas[] = {1, 2, 4};
   const uint32_t smemp[] = {0, 8, 16, 32};
+  // lanes per row, the CTA shape (threads x CTAs per SM: 16 or 20 warps per SM with the
+  // 128- and 96-register builds, or one 512-thread CTA) and tiles per warp interact (they
+  // set how rows split into subtiles and how many warps share an SM), so they are swept
+  // as one grid rather than one at a time
   const uint32_t lanes[] = {8, 16, 32};
-  for (int pass = 0; pass < 2 && st == CUBOID_OK && !mismatch; ++pass) {
-    auto try_dim = [&](auto setter, const uint32_t* vals, int nv) {
-      for (int i = 0; i < nv && st == CUBOID_OK && !mismatch; ++i) {
-        cuboid_tuning c = cur;
-        setter(c, vals[i]);
-        if (c.block_threads * c.ctas_per_sm > 2048) continue;
-        if (std::memcmp(&c, &cur, sizeof(c)) == 0) continue;
-        float ms = 0.f;
-        st = measure(c, &ms);
-        if (st == CUBOID_OK && ms < cur_ms) {
-          cur = c;
-          cur_ms = ms;
-        }
-      }
-    };
-    try_dim([](cuboid_tuning& c, uint32_t v) { c.hot_primes = v; }, hots, 4);
-    // lanes per row and tiles per warp interact (both set how rows split into subtiles):
-    // swept jointly
-    for (int li = 0; li < 3 && st == CUBOID_OK && !mismatch; ++li) {
-      const uint32_t lane_v = lanes[li];
-      try_dim([lane_v](cuboid_tuning& c, uint32_t v) {
-        c.row_lanes = lane_v;
-        c.tiles_per_warp = v;
-      }, tpws, 8);
+  const uint32_t shapes[][2] = {{256, 2}, {320, 2}, {640, 1}, {512, 1}};
+  const uint32_t tpws[] = {2, 4, 8, 16};
+  auto try_one = [&](const cuboid_tuning& c) {
+    if (st != CUBOID_OK || mismatch || std::memcmp(&c, &cur, sizeof(c)) == 0) return;
+    float ms = 0.f;
+    st = measure(c, &ms);
+    if (st == CUBOID_OK && ms < cur_ms) {
+      cur = c;
+      cur_ms = ms;
     }
-    try_dim([](cuboid_tuning& c, uint32_t v) { c.block_threads = v; }, thr, 3);
-    try_dim([](cuboid_tuning& c, uint32_t v) { c.ctas_per_sm = v; }, ctas, 3);
-    try_dim([](cuboid_tuning& c, uint32_t v) { c.smem_primes = v; }, smemp, 4);
+  };
+  auto sweep_hot = [&]() {
+    for (uint32_t v : hots) {
+      cuboid_tuning c = cur;
+      c.hot_primes = v;
+      try_one(c);
+    }
+  };
+  sweep_hot();
+  const cuboid_tuning base = cur;
+  for (uint32_t lv : lanes)
+    for (const auto& sh : shapes)
+      for (uint32_t tv : tpws) {
+        cuboid_tuning c = base;
+        c.row_lanes = lv;
+        c.block_threads = sh[0];
+        c.ctas_per_sm = sh[1];
+        c.tiles_per_warp = tv;
+        if (std::memcmp(&c, &base, sizeof(c)) == 0) continue;
+        try_one(c);
+      }
+  for (uint32_t v : smemp) {
+    cuboid_tuning c = cur;
+    c.smem_primes = v;
+    try_one(c);
   }
+  sweep_hot();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cuboid_result_free(res);
