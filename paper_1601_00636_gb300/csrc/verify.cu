@@ -83,25 +83,39 @@ __host__ __device__ __forceinline__ ull frommont(ull x, const ModConst& M) { ret
 
 // Sign of the integer X with |X| < (prod m_j - 1) / 2 whose residues modulo m_0..m_{K-1}
 // are x[j] (Montgomery form; not all zero): Garner's mixed-radix digits v_j, compared
-// with those of (prod m_j - 1) / 2 from the most significant digit down.  ginv[i][j] is
-// m_i^-1 mod m_j in Montgomery form.
-template <int KM>
-__host__ __device__ __forceinline__ int garner_sign(const ull* x, int K, const ModConst* mods,
-                                                    const ull (*ginv)[kMaxMod]) {
+// with those of (prod m_j - 1) / 2 from the most significant digit down.  mod(j) gives
+// the constants of m_j and ginv(i, j) m_i^-1 mod m_j in Montgomery form (on the device
+// they read the constant bank directly, on the host the probe's arrays).
+template <int KM, class ModF, class GinvF>
+__host__ __device__ __forceinline__ int garner_sign(const ull* x, int K, ModF mod, GinvF ginv) {
   ull v[KM];
-  v[0] = frommont(x[0], mods[0]);
+  v[0] = frommont(x[0], mod(0));
   for (int j = 1; j < K; ++j) {
-    const ModConst M = mods[j];
+    const ModConst M = mod(j);
     ull t = x[j];
-    for (int i = 0; i < j; ++i) t = mmul(msub(t, tomont(v[i], M), M.m), ginv[i][j], M);
+    for (int i = 0; i < j; ++i) t = mmul(msub(t, tomont(v[i], M), M.m), ginv(i, j), M);
     v[j] = frommont(t, M);
   }
   for (int j = K - 1; j >= 0; --j) {
-    const ull h = mods[j].half;
+    const ull h = mod(j).half;
     if (v[j] != h) return v[j] > h ? -1 : 1;
   }
   return 1;
 }
+struct DevMod {
+  __device__ const ModConst& operator()(int j) const { return c_mod[j]; }
+};
+struct DevGinv {
+  __device__ ull operator()(int i, int j) const { return c_ginv[i][j]; }
+};
+struct HostMod {
+  const ModConst* m;
+  __host__ __device__ const ModConst& operator()(int j) const { return m[j]; }
+};
+struct HostGinv {
+  const ull (*g)[kMaxMod];
+  __host__ __device__ ull operator()(int i, int j) const { return g[i][j]; }
+};
 
 // ---------------------------------------------------------------- 192-bit unsigned
 
@@ -176,9 +190,10 @@ __device__ __forceinline__ ull umod_mont(const U192& u, const ModConst& M) {
 
 // ---------------------------------------------------------------- per-pair context
 
-// Coefficient k of R^(d) (d <= k <= 5) sits at cidx(d, k): 20 entries per modulus.
-__host__ __device__ constexpr int cidx(int d, int k) { return (d == 0 ? 0 : d == 1 ? 6 : d == 2 ? 11 : d == 3 ? 15 : 18) + k - d; }
-constexpr int kCoef = 20;
+// Coefficient k of R^(d) (d <= k <= 5) sits at cidx(d, k) = 6 d + k (a plain row-major
+// index; packing the 20 used entries tighter made the indexing cost more than it saved).
+__host__ __device__ constexpr int cidx(int d, int k) { return d * 6 + k; }
+constexpr int kCoef = 30;
 
 // Moduli a survivor with max(p, q) of `bits` bits needs: 61 K >= 37 + 20 bits.
 __host__ __device__ constexpr int moduli_for_bits(int bits) { return (37 + 20 * bits + 60) / 61; }
@@ -279,7 +294,7 @@ __device__ __noinline__ int exact_sign(const Ctx<KM>& C, int d, const U192& u) {
     allzero &= (acc == 0);
   }
   if (allzero) return 0;
-  return garner_sign<KM>(x, C.K, c_mod, c_ginv);
+  return garner_sign<KM>(x, C.K, DevMod{}, DevGinv{});
 }
 
 template <int KM>
@@ -590,7 +605,7 @@ __global__ void k_probe_modarith(uint32_t op, uint32_t j, const ull* a, const ul
       x[k] = tomont(a[(size_t)i * j + k], c_mod[k]);
       zero &= x[k] == 0;
     }
-    out[i] = zero ? 0ull : (ull)(long long)garner_sign<kMaxMod>(x, (int)j, c_mod, c_ginv);
+    out[i] = zero ? 0ull : (ull)(long long)garner_sign<kMaxMod>(x, (int)j, DevMod{}, DevGinv{});
   }
 }
 
@@ -645,7 +660,7 @@ extern "C" int cuboid_probe_modarith(uint32_t op, uint32_t j, const uint64_t* a,
           x[k] = tomont(a[(size_t)i * j + k], mods[k]);
           zero &= x[k] == 0;
         }
-        out[i] = zero ? 0ull : (ull)(long long)garner_sign<kMaxMod>(x, (int)j, mods, ginv);
+        out[i] = zero ? 0ull : (ull)(long long)garner_sign<kMaxMod>(x, (int)j, HostMod{mods}, HostGinv{ginv});
       }
     }
     return CUBOID_OK;
