@@ -330,11 +330,13 @@ struct Isolator {
   }
 
   // FP64 proposal of the sign change of R^(d) inside [lo, hi] (sign sa at lo).
+  // Bisection stops once the bracket is narrower than the exact step uses (the proposal
+  // is widened by max(4, |g| 2^-36) before exact signs check it): width <= max(1, 2^-40 b).
   __device__ __noinline__ double guess(int d, const U192& lo, const U192& hi, int sa) {
     double a = utod(lo), b = utod(hi);
     for (int it = 0; it < 400; ++it) {
       const double m = 0.5 * (a + b);
-      if (!(m > a && m < b)) break;
+      if (!(m > a && m < b) || b - a <= fmax(1.0, b * 0x1p-40)) break;
       const double f = fval(*C, d, m);
       if (f == 0.0) return m;
       if ((f < 0.0 ? -1 : 1) == sa) a = m; else b = m;
