@@ -691,7 +691,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
       if (onA) {
 #pragma unroll
         for (int i = 0; i < kFacRegs; ++i) {  // inert entries give an empty mask
-          if (G == 32 && (uint32_t)i >= nfo) break;  // whole-warp rows: nfo is the warp's
+          // whole-warp rows (nfo is the warp's): the second pair of slots only for rows with
+          // three or more odd factors (a test per slot costs more than the inert slot it saves)
+          if (G == 32 && i == 2 && nfo <= 2u) break;
           const uint4 fc = s_fac[i];          // {f, (128 G) mod f, table base, cap}
           const uint32_t mi = fma_add(fc.z, min(tf[i], fc.w), one);
           const uint4 mk = CUBOID_IDX_OK(mi < kMaskTab, a.hdr, 4u) ? s_mtab[mi] : make_uint4(0u, 0u, 0u, 0u);
