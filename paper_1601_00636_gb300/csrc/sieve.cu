@@ -482,8 +482,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
 
     // ---- distinct odd prime factors of x (trial division shared by the group's lanes)
     // Each lane tests one trial prime per batch; a lane that divides x writes its factor
-    // entry {f, (128 G) mod f, mask table base, cap} and its reciprocal, and divides its
-    // prime power out of the cofactor through a product over the group.
+    // entry {f - y, -y, mask table base, cap} (y = (128 G) mod f) and its reciprocal, and
+    // divides its prime power out of the cofactor through a product over the group.
     uint32_t nfo = 0;  // uniform in the group
     bool has2 = false;
     uint32_t big = 1;  // a prime factor above 2^31 left out of the masks (x itself), or 1
@@ -526,7 +526,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           const uint32_t pos = nfo + __popc(bal & lanemask_lt);
           const uint32_t f = tp.f;
           if (CUBOID_IDX_OK(pos < kMaxFactors, a.hdr, 5u)) {
-            s_fac[pos] = make_uint4(f, mod_min(kStride, f, tp.lim), f < kPeriodicBelow ? s_foff[f] : kBitTab,
+            const uint32_t y = mod_min(kStride, f, tp.lim);
+            s_fac[pos] = make_uint4(f - y, 0u - y, f < kPeriodicBelow ? s_foff[f] : kBitTab,
                                     f < kPeriodicBelow ? f - 1 : 128u);
             s_fmag[pos] = tp.lim;  // floor(2^32 / f) for odd f > 1
             if constexpr (kWide) s_fyb[pos] = (uint32_t)(a.y_base % f);
@@ -546,7 +547,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
       if (live && m > 1 && (kWide || m <= 0x80000000u)) {
         if (gl == 0 && CUBOID_IDX_OK(nfo < kMaxFactors, a.hdr, 5u)) {
           const uint32_t mag = 0xFFFFFFFFu / m;
-          s_fac[nfo] = make_uint4(m, mod_min(kStride, m, mag), m < kPeriodicBelow ? s_foff[m] : kBitTab,
+          const uint32_t y = mod_min(kStride, m, mag);
+          s_fac[nfo] = make_uint4(m - y, 0u - y, m < kPeriodicBelow ? s_foff[m] : kBitTab,
                                   m < kPeriodicBelow ? m - 1 : 128u);
           s_fmag[nfo] = mag;
           if constexpr (kWide) s_fyb[nfo] = (uint32_t)(a.y_base % m);
@@ -568,7 +570,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     for (int i = 0; i < kFacRegs; ++i) {
       tf[i] = 128u;  // inert entry
       if ((uint32_t)i < nfo) {
-        const uint32_t f = s_fac[i].x;
+        const uint32_t f = s_fac[i].x - s_fac[i].y;
         uint32_t r = mod_min(y0f, f, s_fmag[i]);
         if constexpr (kWide) {  // (y_base + y0) mod f; f may exceed 2^31
           const unsigned long long rr = (unsigned long long)r + s_fyb[i];
@@ -616,7 +618,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         uint32_t sign = 0;
         for (uint32_t b = 0; b < np && d <= Y1; ++b) {
           if (!((set >> b) & 1u)) continue;
-          const uint32_t f = b < nfo ? s_fac[b].x : (b == nfo && has2 ? 2u : big);
+          const uint32_t f = b < nfo ? s_fac[b].x - s_fac[b].y : (b == nfo && has2 ? 2u : big);
           d *= f;
           sign ^= 1u;
         }
@@ -684,7 +686,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     uint32_t wb = wbeg + 2 * gl;
     for (uint32_t j = 0; j < maxit; ++j, wb += 2 * G) {
       const uint32_t wA = wb, wB = wb + 1;  // the lane's pair of adjacent words
-      const bool onA = j < nit && wA <= wend, onB = j < nit && wB <= wend;
+      // (whole-warp rows: every lane runs nit = maxit iterations)
+      const bool onA = (G == 32 || j < nit) && wA <= wend, onB = (G == 32 || j < nit) && wB <= wend;
       // bits to exclude: y sharing a prime factor with x (128-bit masks from the image for
       // both words at once), even y for even x, then the range edges and the diagonal
       uint4 m = make_uint4(even_bits, even_bits, even_bits, even_bits);
@@ -694,28 +697,29 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           // whole-warp rows (nfo is the warp's): the second pair of slots only for rows with
           // three or more odd factors (a test per slot costs more than the inert slot it saves)
           if (G == 32 && i == 2 && nfo <= 2u) break;
-          const uint4 fc = s_fac[i];          // {f, (128 G) mod f, table base, cap}
+          const uint4 fc = s_fac[i];          // {f - y, -y, table base, cap}, y = (128 G) mod f
           const uint32_t mi = fma_add(fc.z, min(tf[i], fc.w), one);
           const uint4 mk = CUBOID_IDX_OK(mi < kMaskTab, a.hdr, 4u) ? s_mtab[mi] : make_uint4(0u, 0u, 0u, 0u);
           m.x |= mk.x;
           m.y |= mk.y;
           m.z |= mk.z;
           m.w |= mk.w;
-          // the lane's next pair starts 128 G further on: t <- (t - 128 G) mod f, the
-          // smaller of t - y (wraps when t < y) and t - y + f (f <= 2^31, so no wrap)
+          // the lane's next pair starts 128 G further on: t <- (t - y) mod f, the smaller
+          // of t - y (wraps when t < y) and t - y + f (f <= 2^31, so no wrap)
           if constexpr (kWide)  // a factor above 2^31 (x itself) has multiples 2x, 3x, ... here
-            tf[i] = tf[i] >= fc.y ? tf[i] - fc.y : tf[i] - fc.y + fc.x;
+            tf[i] = tf[i] >= 0u - fc.y ? tf[i] + fc.y : tf[i] + fc.x;
           else
-            tf[i] = min(fma_add(tf[i], 0u - fc.y, one), fma_add(tf[i], fc.x - fc.y, one));
+            tf[i] = min(fma_add(tf[i], fc.y, one), fma_add(tf[i], fc.x, one));
         }
         for (uint32_t i = kFacRegs; i < nfo; ++i) {
           const uint4 fc = s_fac[i];
-          uint32_t s = mod_min(wA << 6, fc.x, s_fmag[i]);
+          const uint32_t f = fc.x - fc.y;
+          uint32_t s = mod_min(wA << 6, f, s_fmag[i]);
           if constexpr (kWide) {
             const unsigned long long ss = (unsigned long long)s + s_fyb[i];
-            s = (uint32_t)(ss >= fc.x ? ss - fc.x : ss);
+            s = (uint32_t)(ss >= f ? ss - f : ss);
           }
-          const uint32_t t = s ? fc.x - s : 0u;
+          const uint32_t t = s ? f - s : 0u;
           const uint32_t mi = fc.z + min(t, fc.w);
           const uint4 mk = CUBOID_IDX_OK(mi < kMaskTab, a.hdr, 4u) ? s_mtab[mi] : make_uint4(0u, 0u, 0u, 0u);
           m.x |= mk.x;
