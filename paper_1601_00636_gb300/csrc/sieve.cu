@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     // x even: y0 is even, so the even y (excluded) sit at the even bits
     const uint32_t even_bits = has2 ? 0x55555555u : 0u;
     // Interior pairs of words (neither word on a range edge, both in the subtile) have
-    // their first word in [int_lo, int_lo + int_span]; the others take the edge path,
+    // their first word in [int_base, int_base + int_span]; the others take the edge path,
     // as do the pairs holding the diagonal word.
     const long long int_hi = (long long)(wend < whi ? wend + 1 : whi) - 2;  // last interior first word
     const long long int_lo = (long long)wlo + 1;
@@ -683,15 +683,30 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
                              st_warpsteps, false);
       }
     };
-    uint32_t wb = wbeg + 2 * gl;
+    // The same window in iterations: this lane's pairs start at words wb0 + 2 G j, the
+    // interior ones for j in [j_lo, j_lo + j_span] (none: j_lo = 2^32 - 1, j_span = 0), and
+    // the pair holding the diagonal word is iteration j_d (none: 2^32 - 1), so the word
+    // loop tests its iteration number instead of the words.
+    const uint32_t wb0 = wbeg + 2 * gl;
+    uint32_t j_lo = 0xFFFFFFFFu, j_span = 0u;
+    if (has_interior && int_base + int_span >= wb0) {
+      const uint32_t first = int_base > wb0 ? (int_base - wb0 + 2 * G - 1) / (2 * G) : 0u;
+      const uint32_t last = (int_base + int_span - wb0) / (2 * G);
+      if (first <= last) {
+        j_lo = first;
+        j_span = last - first;
+      }
+    }
+    uint32_t j_d = 0xFFFFFFFFu;
+    if (diag_in && dword >= wb0 && (dword - wb0) % (2 * G) <= 1u) j_d = (dword - wb0) / (2 * G);
+    uint32_t wb = wb0;
     for (uint32_t j = 0; j < maxit; ++j, wb += 2 * G) {
       const uint32_t wA = wb, wB = wb + 1;  // the lane's pair of adjacent words
-      // (whole-warp rows: every lane runs nit = maxit iterations)
-      const bool onA = (G == 32 || j < nit) && wA <= wend, onB = (G == 32 || j < nit) && wB <= wend;
       // bits to exclude: y sharing a prime factor with x (128-bit masks from the image for
-      // both words at once), even y for even x, then the range edges and the diagonal
+      // both words at once), even y for even x, then the range edges and the diagonal.  A
+      // lane whose pair lies past the subtile computes masks the edge path then overwrites.
       uint4 m = make_uint4(even_bits, even_bits, even_bits, even_bits);
-      if (onA) {
+      {
 #pragma unroll
         for (int i = 0; i < kFacRegs; ++i) {  // inert entries give an empty mask
           // whole-warp rows (nfo is the warp's): the second pair of slots only for rows with
@@ -729,7 +744,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         }
       }
       // (a pair with a word outside the subtile, or of an idle group, is an edge pair too)
-      if (!onB || fma_add(wA, 0u - int_base, one) > int_span || (diag_in && (wA == dword || wB == dword))) {
+      if (j - j_lo > j_span || j == j_d) {
+        // (whole-warp rows: every lane runs nit = maxit iterations)
+        const bool onA = (G == 32 || j < nit) && wA <= wend, onB = (G == 32 || j < nit) && wB <= wend;
         edge_word(wA, onA, m.x, m.y);
         edge_word(wB, onB, m.z, m.w);
       }

@@ -141,7 +141,7 @@ def test_autotune_keeps_results(env, tmp_path):
     try:
         cache = str(tmp_path / "tune.txt")
         tune, ms = cb.cuboid_autotune(t, g["ranges"], cb.MODE_BATCHED, stream, cache)
-        assert ms > 0 and tune["block_threads"] in (256, 512)
+        assert ms > 0 and tune["block_threads"] in (256, 320, 512, 640)
         assert cb.cuboid_tables_get_tuning(t) == tune
         tune2, ms2 = cb.cuboid_autotune(t, g["ranges"], cb.MODE_BATCHED, stream, cache)   # cache hit
         assert tune2 == tune and abs(ms2 - ms) < 1e-3
