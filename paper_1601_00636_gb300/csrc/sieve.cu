@@ -18,6 +18,7 @@
 // Tiles come from a device queue (one atomic per tile), so one kernel serves one range
 // per launch and thousands of ranges per launch.
 #include <mutex>
+#include <type_traits>
 
 #include "cuboid_internal.cuh"
 
@@ -699,6 +700,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     }
     uint32_t j_d = 0xFFFFFFFFu;
     if (diag_in && dword >= wb0 && (dword - wb0) % (2 * G) <= 1u) j_d = (dword - wb0) / (2 * G);
+    // The word loop, compiled twice: with the pair totals left to the Moebius count above,
+    // or counted per pair of words (a flag tested in every iteration cost 2 %).
+    auto word_loop = [&](auto by_mobius) {
+    constexpr bool kMob = decltype(by_mobius)::value;
     uint32_t wb = wb0;
     for (uint32_t j = 0; j < maxit; ++j, wb += 2 * G) {
       const uint32_t wA = wb, wB = wb + 1;  // the lane's pair of adjacent words
@@ -751,7 +756,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         edge_word(wB, onB, m.z, m.w);
       }
       uint32_t alA = ~m.x, ahA = ~m.y, alB = ~m.z, ahB = ~m.w;
-      if (!mob) {  // pairs of this pair of words: 128 minus the excluded bits
+      if constexpr (!kMob) {  // pairs of this pair of words: 128 minus the excluded bits
         tile_pairs = fma_add(tile_pairs, 128u, one);
         tile_pairs = fma_sub(tile_pairs, __popc(m.x), one);
         tile_pairs = fma_sub(tile_pairs, __popc(m.y), one);
@@ -784,6 +789,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
       if (kSteps) st_warpsteps += 2 * K;
       enqueue2(alA, ahA, alB, ahB, wA << 6);
     }
+    };
+    if (mob) word_loop(std::true_type{});
+    else word_loop(std::false_type{});
     if constexpr (K > 0) {
       if ((uint32_t)(K - 1) > ws.imax) ws.imax = (uint32_t)(K - 1);
     }
