@@ -200,14 +200,16 @@ def phi_sum(n_max: int, lo: int = 2) -> int:
 
 
 PROBE_KINDS = {0: ("alu_tops", 48), 1: ("lookup_mix_tops", 96), 2: ("lop3", 16), 3: ("funnel_shift", 16),
-               4: ("popc_plus_mad", 32), 5: ("mad_lo", 16), 6: ("mad_wide", 16), 7: ("mad_hi", 16)}
+               4: ("popc_plus_mad", 32), 5: ("mad_lo", 16), 6: ("mad_wide", 16), 7: ("mad_hi", 16),
+               8: ("add_min", 16)}
 
 
 def int_issue_probe(cb, torch, stream, sm_mhz: float = 2070.0):
     """Measured integer issue rates: a dependency-free add/shift/xor stream on every SM
     (alu_tops), the sieve's lookup mix (shared-memory load pair, funnel shift, and, popc,
     xor), and one-instruction streams (lop3, funnel shift, popc + mad, mad.lo, mad.wide,
-    mad.hi) as lane-ops per clock per SM at the given clock."""
+    mad.hi, the add-then-minimum of the residue steps) as lane-ops per clock per SM at the
+    given clock."""
     sms = cb.cuboid_device_sms()
     blocks, threads, iters = sms * 8, 256, 4096
     sink = torch.empty(blocks * threads, dtype=torch.int32, device="cuda")

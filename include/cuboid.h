@@ -528,7 +528,8 @@ int cuboid_server_destroy(cuboid_server* s, uint32_t timeout_ms);
  * `iters` iterations of 16 independent 32-bit integer ops (kind 0: add/shift/xor mix,
  * kind 1: the sieve's lookup mix with shared-memory loads; kinds 2-7 one instruction per
  * chain step: 2 lop3, 3 funnel shift, 4 popc followed by one mad.lo, 5 mad.lo, 6 mad.wide
- * (32 x 32 + 64 bits), 7 mad.hi).  sink_dev: device buffer of blocks*threads uint32
+ * (32 x 32 + 64 bits), 7 mad.hi, 8 the add-then-minimum min(a + b, c) of __viaddmin_u32,
+ * which the sieve's residue steps use).  Kind > 8: EINVAL.  sink_dev: device buffer of blocks*threads uint32
  * (defeats dead-code elimination).  Asynchronous. */
 int cuboid_probe_int_issue(uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
                            uint32_t* sink_dev, void* stream);

@@ -1129,7 +1129,8 @@ __device__ __forceinline__ uint32_t op_madhi(uint32_t a, uint32_t b, uint32_t c)
 // kind 0: 16 independent chains of add / shift / xor (three 32-bit integer ops each).
 // kind 1: the sieve's lookup mix: shared-memory load pair, funnel shift, and, popc, xor.
 // kinds 2-7: one instruction per chain step: lop3, funnel shift, popc (+ one mad.lo),
-// mad.lo, mad.wide (32 x 32 + 64), mad.hi.
+// mad.lo, mad.wide (32 x 32 + 64), mad.hi; kind 8: the add-then-minimum min(a + b, c) of
+// __viaddmin_u32 (one instruction on GPUs with the DPX instructions).
 __global__ void k_probe(uint32_t kind, uint32_t iters, uint32_t* sink) {
   __shared__ uint32_t tab[1024];
   for (uint32_t i = threadIdx.x; i < 1024; i += blockDim.x) tab[i] = i * 2654435761u;
@@ -1174,6 +1175,8 @@ __global__ void k_probe(uint32_t kind, uint32_t iters, uint32_t* sink) {
       CUBOID_PROBE_LOOP(a[i] = op_mad(a[i], k1, k2))
     } else if (kind == 6) {
       CUBOID_PROBE_LOOP(w[i] = op_madwide((uint32_t)w[i], k1, w[i]))
+    } else if (kind == 8) {
+      CUBOID_PROBE_LOOP(a[i] = __viaddmin_u32(a[i], k1, k2))
     } else {
       CUBOID_PROBE_LOOP(a[i] = op_madhi(a[i], k1, k2))
     }
@@ -1191,7 +1194,7 @@ __global__ void k_probe(uint32_t kind, uint32_t iters, uint32_t* sink) {
 
 extern "C" int cuboid_probe_int_issue(uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
                                       uint32_t* sink_dev, void* stream) {
-  if (kind > 7 || blocks == 0 || threads == 0 || threads > 1024 || threads % 32 || !sink_dev)
+  if (kind > 8 || blocks == 0 || threads == 0 || threads > 1024 || threads % 32 || !sink_dev)
     return CUBOID_EINVAL;
   k_probe<<<blocks, threads, 0, (cudaStream_t)stream>>>(kind, iters, sink_dev);
   return status_from_cuda(cudaGetLastError());

@@ -126,10 +126,11 @@ __device__ __forceinline__ void lds5(uint32_t ad, uint32_t& w0, uint32_t& w1, ui
 }
 
 // n mod r for any 32-bit n, with magic = floor(2^32 / r): n - floor(n*magic/2^32) r is
-// n mod r or n mod r + r, and the unsigned minimum with itself minus r picks the residue.
+// n mod r or n mod r + r, and the unsigned minimum with itself minus r (one add-and-minimum)
+// picks the residue.
 __device__ __forceinline__ uint32_t mod_min(uint32_t n, uint32_t r, uint32_t magic) {
   const uint32_t e = n - __umulhi(n, magic) * r;
-  return min(e, e - r);
+  return __viaddmin_u32(e, 0u - r, e);
 }
 
 // Up to 32 queued words {x, y0, alive lo, alive hi} (one per lane) of range `range` go
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
 
     // ---- distinct odd prime factors of x (trial division shared by the group's lanes)
     // Each lane tests one trial prime per batch; a lane that divides x writes its factor
-    // entry {f - y, -y, mask table base, cap} (y = (128 G) mod f) and its reciprocal, and
+    // entry {f - y, -y, mask table base, base + cap} (y = (128 G) mod f) and its reciprocal, and
     // divides its prime power out of the cofactor through a product over the group.
     uint32_t nfo = 0;  // uniform in the group
     bool has2 = false;
@@ -528,8 +529,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           const uint32_t f = tp.f;
           if (CUBOID_IDX_OK(pos < kMaxFactors, a.hdr, 5u)) {
             const uint32_t y = mod_min(kStride, f, tp.lim);
-            s_fac[pos] = make_uint4(f - y, 0u - y, f < kPeriodicBelow ? s_foff[f] : kBitTab,
-                                    f < kPeriodicBelow ? f - 1 : 128u);
+            const uint32_t base = f < kPeriodicBelow ? s_foff[f] : kBitTab;
+            s_fac[pos] = make_uint4(f - y, 0u - y, base, base + (f < kPeriodicBelow ? f - 1 : 128u));
             s_fmag[pos] = tp.lim;  // floor(2^32 / f) for odd f > 1
             if constexpr (kWide) s_fyb[pos] = (uint32_t)(a.y_base % f);
           }
@@ -549,8 +550,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         if (gl == 0 && CUBOID_IDX_OK(nfo < kMaxFactors, a.hdr, 5u)) {
           const uint32_t mag = 0xFFFFFFFFu / m;
           const uint32_t y = mod_min(kStride, m, mag);
-          s_fac[nfo] = make_uint4(m - y, 0u - y, m < kPeriodicBelow ? s_foff[m] : kBitTab,
-                                  m < kPeriodicBelow ? m - 1 : 128u);
+          const uint32_t base = m < kPeriodicBelow ? s_foff[m] : kBitTab;
+          s_fac[nfo] = make_uint4(m - y, 0u - y, base, base + (m < kPeriodicBelow ? m - 1 : 128u));
           s_fmag[nfo] = mag;
           if constexpr (kWide) s_fyb[nfo] = (uint32_t)(a.y_base % m);
         }
@@ -559,7 +560,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         big = m;
       }
       // inert entries up to kFacRegs: offset 128 that never moves, empty mask
-      if (gl < (uint32_t)kFacRegs && gl >= nfo) s_fac[gl] = make_uint4(1u, 0u, kBitTab, 128u);
+      if (gl < (uint32_t)kFacRegs && gl >= nfo) s_fac[gl] = make_uint4(1u, 0u, kBitTab, kBitTab + 128u);
       __syncwarp();
     }
     // Each lane sieves pairs of adjacent words (128 values): pair p of the subtile covers
@@ -717,8 +718,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           // whole-warp rows (nfo is the warp's): the second pair of slots only for rows with
           // three or more odd factors (a test per slot costs more than the inert slot it saves)
           if (G == 32 && i == 2 && nfo <= 2u) break;
-          const uint4 fc = s_fac[i];          // {f - y, -y, table base, cap}, y = (128 G) mod f
-          const uint32_t mi = fma_add(fc.z, min(tf[i], fc.w), one);
+          const uint4 fc = s_fac[i];          // {f - y, -y, table base, base + cap}, y = (128 G) mod f
+          // base + min(t, cap) as one add-and-minimum, min(t + base, base + cap): in 32-bit
+          // ranges t < f <= 2^31, so t + base does not wrap
+          const uint32_t mi = kWide ? fc.z + min(tf[i], fc.w - fc.z) : __viaddmin_u32(tf[i], fc.z, fc.w);
           const uint4 mk = CUBOID_IDX_OK(mi < kMaskTab, a.hdr, 4u) ? s_mtab[mi] : make_uint4(0u, 0u, 0u, 0u);
           m.x |= mk.x;
           m.y |= mk.y;
@@ -729,7 +732,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
           if constexpr (kWide)  // a factor above 2^31 (x itself) has multiples 2x, 3x, ... here
             tf[i] = tf[i] >= 0u - fc.y ? tf[i] + fc.y : tf[i] + fc.x;
           else
-            tf[i] = min(fma_add(tf[i], fc.y, one), fma_add(tf[i], fc.x, one));
+            tf[i] = __viaddmin_u32(tf[i], fc.y, fma_add(tf[i], fc.x, one));
         }
         for (uint32_t i = kFacRegs; i < nfo; ++i) {
           const uint4 fc = s_fac[i];
@@ -740,7 +743,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
             s = (uint32_t)(ss >= f ? ss - f : ss);
           }
           const uint32_t t = s ? f - s : 0u;
-          const uint32_t mi = fc.z + min(t, fc.w);
+          const uint32_t mi = kWide ? fc.z + min(t, fc.w - fc.z) : __viaddmin_u32(t, fc.z, fc.w);
           const uint4 mk = CUBOID_IDX_OK(mi < kMaskTab, a.hdr, 4u) ? s_mtab[mi] : make_uint4(0u, 0u, 0u, 0u);
           m.x |= mk.x;
           m.y |= mk.y;
@@ -771,7 +774,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
         const uint32_t s = sh[h];
         // next pair: + (128 G) mod r; the smaller of s + step and s + step - r (which
         // wraps when s + step < r) is the residue
-        sh[h] = min(fma_add(s, a.hot_step[h], one), fma_add(s, a.hot_step_m[h], one));
+        sh[h] = __viaddmin_u32(s, a.hot_step[h], fma_add(s, a.hot_step_m[h], one));
         // shared byte address of word s / 32 of the row (s >> 5 by a multiply-high)
         const uint32_t ad = fma_mad(mulhi_fma(s, 1u << 27), 4u, rb4[h]);
         uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0;

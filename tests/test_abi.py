@@ -59,6 +59,7 @@ def test_null_handles_are_rejected(lib_path):
     assert lib.cuboid_sieve(None, 1, 2, 1, 2, 0, None, None) == cb.ENOTABLES
     assert lib.cuboid_server_destroy(None, 0) == cb.EINVAL
     assert lib.cuboid_probe_int_issue(5, 1, 32, 1, None, None) == cb.EINVAL
+    assert lib.cuboid_probe_int_issue(9, 1, 32, 1, 16, None) == cb.EINVAL
     assert lib.cuboid_sieve_wide(None, None, 0, None, None) == cb.ENOTABLES
     assert lib.cuboid_result_get_wide(None, 0, None, None, None, None, None, None) == cb.EINVAL
     assert lib.cuboid_region_scan_wide(None, 1, 0, 2, None, None, None, 0, None, 0, None) == cb.ENOTABLES
