@@ -18,7 +18,7 @@ constexpr uint32_t kPrimeLimit = 9697;     // r < 9697: the bound derived below 
 constexpr uint32_t kStageSpins = 1u << 22;    // polls of a CTA's staging barrier before it gives up
 constexpr uint32_t kMaxChunkWords = 32768;   // 64-value words per subtile: at most 2^21 pairs
 constexpr uint32_t kMaxFactors = 10;       // distinct primes of a 32-bit integer <= 9
-constexpr uint32_t kSieveRevision = 21;    // part of the autotuner's cache key: bump when the kernel changes
+constexpr uint32_t kSieveRevision = 22;    // part of the autotuner's cache key: bump when the kernel changes
 
 // Coprimality mask image: for each odd prime f < 128 and offset t in [0, f) the 128-bit
 // mask of bits t, t + f, t + 2f, ... (as four uint32 quarters: two adjacent 64-value
@@ -68,7 +68,7 @@ constexpr uint32_t kRowsQ = 0x80000000u;
 
 // Device header of a result object.
 struct DevHeader {
-  unsigned long long cursor;       // next tile of the running launch
+  unsigned long long cursor;       // tiles handed out after each warp's first (fixed) tile
   unsigned long long total_tiles;  // tiles of the running launch
   unsigned long long n_surv;       // survivors found (may exceed the capacity)
   unsigned long long n_roots;      // roots found (may exceed the capacity)

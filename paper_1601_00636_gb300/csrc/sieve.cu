@@ -394,9 +394,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
     __syncwarp();
   };
 
-  unsigned long long next = 0;
-  if (lane == 0) next = atomicAdd(&a.hdr->cursor, 1ull);
-  next = __shfl_sync(FULL, next, 0);
+  // The first tile of every warp is fixed (tile CTA x warps + warp: no atomic on the
+  // shared cursor at the start, when every warp would ask at once); the cursor hands out
+  // the tiles after those.
+  const unsigned long long first_tiles = (unsigned long long)gridDim.x * warps;
+  unsigned long long next = (unsigned long long)blockIdx.x * warps + wid;
   TilePlan P1{};  // a single-range launch reads its plan once
   if (a.self_plan) P1 = s_self_plan;
   else if (count == 1) P1 = a.plan[a.range_first];
@@ -404,7 +406,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sieve(SieveArgs a) {
   for (;;) {
     const unsigned long long tile = next;
     if (tile >= total) break;
-    if (lane == 0) next = atomicAdd(&a.hdr->cursor, 1ull);  // prefetch the next tile
+    if (lane == 0) next = first_tiles + atomicAdd(&a.hdr->cursor, 1ull);  // prefetch the next tile
 
     uint32_t k = a.range_first;
     if (count > 1) {  // first range with tile_end > tile
