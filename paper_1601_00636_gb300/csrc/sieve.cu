@@ -15,8 +15,8 @@
 // their counts kept as per-lane sums; words still alive afterwards go to a per-warp queue
 // and are finished 32 at a time with a warp-uniform early exit.  Survivors (alive bits
 // after the last prime) are compacted with a warp prefix sum and one atomic per warp.
-// Tiles come from a device queue (one atomic per tile), so one kernel serves one range
-// per launch and thousands of ranges per launch.
+// Tiles come from a device queue (each warp's first tile fixed, then one atomic per tile),
+// so one kernel serves one range per launch and thousands of ranges per launch.
 #include <mutex>
 #include <type_traits>
 
