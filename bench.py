@@ -571,10 +571,15 @@ def measure(cb, torch, dist, stream, flush, spec, args, world, rank, tables=None
     prof = profile_record(spec["name"])
     executed = None
     if prof.get("inst_executed_per_launch"):
+        # every executed instruction, on any pipe, against the issue slots (one warp
+        # instruction per clock per SM sub-partition): not against the ALU pipe alone
         ex = prof["inst_executed_per_launch"] * 32 / (per_launch_ms / 1e3) / 1e12
-        executed = {"tops": ex, "frac": ex / peak, "issue_active_pct_ncu": prof.get("issue_active_pct"),
+        issue_peak = sms * 4 * 32 * sm_max * 1e6 / 1e12
+        executed = {"tops": ex, "issue_peak_tops": issue_peak, "frac_of_issue_slots": ex / issue_peak,
+                    "issue_active_pct_ncu": prof.get("issue_active_pct"),
                     "alu_pipe_pct_ncu": prof.get("alu_pipe_pct"),
-                    "note": "warp instructions per launch from the committed ncu record x 32 lanes / live launch time"}
+                    "note": "warp instructions per launch from the committed ncu record x 32 lanes / live launch "
+                            "time, against 4 issue slots x 32 lanes per clock per SM (instructions of every pipe)"}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": prof.get("dram_bytes_per_launch"), "kernel": "k_sieve", "launch_ms": per_launch_ms,
                 "peak_note": f"{sms} SMs x {INT_LANES_PER_SM_CLK} int32 logic lanes per clock (16 per SM "
